@@ -1,0 +1,173 @@
+/*
+ * hsearch.h -- C ABI of the GB300 heuristic protein database search.
+ *
+ * The method is the randomised sliding-subsequence alignment of Nag &
+ * Karforma, "A Space-Efficient Approach towards Distantly Homologous Protein
+ * Similarity Searches" (arXiv 1508.06561), in its database-search form:
+ * one query is aligned against every database sequence (Sec. III.B.3), each
+ * pair with O(1) auxiliary state (Sec. III.B.4), the pairs are ranked by score
+ * (Sec. IV) and the best k are returned with their alignments (Fig. 1).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an int status (HS_OK == 0); nothing is thrown.
+ *   - Sequences are residue codes (uint8) in the 24-letter BLOSUM62 order
+ *     "ARNDCQEGHILKMFPSTWYVBZX*" (codes 0..23); hs_encode converts ASCII.
+ *   - Pointers documented "host" must be host memory; "device" pointers must
+ *     be device memory of the current CUDA device.  `stream` is a
+ *     cudaStream_t (NULL = the legacy default stream).
+ *   - Outputs are caller-allocated; the library keeps no reference to them.
+ *   - Results are a pure function of (database, query, params, seed): the
+ *     random draws of a pair are keyed by its original database index.
+ *   - Hits are ordered by score descending, then database index ascending.
+ *   - Scores are int32.  Sequences may be at most HS_MAX_SEQ_LEN long and
+ *     penalties at most HS_MAX_PENALTY, which keeps every score in range.
+ */
+#ifndef HSEARCH_H
+#define HSEARCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define HS_OK        0
+#define HS_EINVAL    1   /* bad argument (sizes, codes, params, offsets)        */
+#define HS_ENOMEM    2   /* device or host allocation failed                    */
+#define HS_ECUDA     3   /* a CUDA call failed (no device, launch error, ...)   */
+#define HS_ETOOLONG  4   /* a sequence or the query exceeds a supported length  */
+#define HS_ETIMEOUT  5   /* a bounded device wait ran out                       */
+#define HS_ETRUNC    6   /* an output buffer (ops, workspace) is too small      */
+#define HS_EINTERNAL 7   /* replay disagreed with the scan (never expected)     */
+
+#define HS_MAX_SEQ_LEN  1000000
+#define HS_MAX_QUERY_LEN 2048
+#define HS_MAX_PENALTY  1000
+#define HS_MAX_K        4096
+
+#define HS_MODE_DB   0   /* Sec. III.B.3 b: small slides inside large only     */
+
+/* alignment run-length ops: op = v & 3, run length = v >> 2 */
+#define HS_OP_M 0u       /* query letter against target letter                 */
+#define HS_OP_I 1u       /* query letter against a gap in the target           */
+#define HS_OP_D 2u       /* target letter against a gap in the query           */
+
+/* ---- parameters (Sec. III.B.1; defaults of Sec. IV) --------------------
+ * pgp, gop, gep : periphery, gap-open and gap-extend penalties, >= 0,
+ *                 subtracted; an interior gap run of n costs gop+(n-1)*gep.
+ * rounds        : AlignSequences' Rounds (>= 1; 1 in database search).
+ * lfactor_q16, sfactor_q16, minfactor_q16 : LFactor, SFactor, MinFactor in
+ *                 Q16 fixed point (65536 == 1.0), each in [0, 65536].
+ * mode          : HS_MODE_DB.
+ * matrix        : host pointer to a 24x24 row-major int8 table, entry
+ *                 [a][b] scoring query letter a against target letter b;
+ *                 must be symmetric.  NULL selects the built-in BLOSUM62.  */
+typedef struct {
+    int32_t pgp, gop, gep, rounds;
+    uint32_t lfactor_q16, sfactor_q16, minfactor_q16;
+    int32_t mode;
+    const int8_t *matrix;
+} hs_params;
+
+/* One ranked hit.  The alignment is ops[ops_offset .. ops_offset+ops_len)
+ * of the ops buffer and covers both full sequences (its M+I runs sum to the
+ * query length, its M+D runs to the target length).  [q_begin, q_end) and
+ * [t_begin, t_end) bound the letter-pair columns (all -1 if there are none).*/
+typedef struct {
+    int64_t db_index;
+    int32_t score;
+    int32_t q_begin, q_end, t_begin, t_end;
+    int32_t ops_len;
+    int64_t ops_offset;
+} hs_hit;
+
+typedef struct hs_db hs_db;   /* opaque; owns the device copy of a database */
+
+/* The paper's parameter set (Sec. IV): PGP=0, GOP=10, GEP=5, LFactor=0.5,
+ * SFactor=1, MinFactor=0.5, Rounds=1 (Sec. III.B.3 a), BLOSUM62. */
+void hs_params_default(hs_params *p);
+
+/* ASCII letters -> codes; lower case accepted, any other byte becomes X.
+ * ascii and codes_out are host buffers of n bytes. */
+int hs_encode(const char *ascii, int64_t n, uint8_t *codes_out);
+
+/* Copies the built-in BLOSUM62 (Henikoff & Henikoff 1992; the matrix of
+ * Sec. III.A / III.B.5) into the host buffer out[576]. */
+int hs_builtin_matrix(int8_t *out);
+
+/* Checks a parameter block and its matrix without touching the GPU. */
+int hs_params_check(const hs_params *p);
+
+/* Database load (the packing step of the search: once per database).
+ * codes: host, offsets[n_seqs] residue codes; sequence i is
+ * codes[offsets[i] .. offsets[i+1]); offsets: host, n_seqs+1 entries,
+ * offsets[0] == 0, non-decreasing; empty sequences are allowed.  The
+ * library copies both to the device (the caller keeps its buffers), orders
+ * the sequences by length on the device for scheduling, and returns a
+ * handle in *out.  Errors: HS_EINVAL (bad offsets or codes >= 24),
+ * HS_ETOOLONG (a sequence longer than HS_MAX_SEQ_LEN), HS_ENOMEM, HS_ECUDA. */
+int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs,
+               void *stream, hs_db **out);
+
+/* Number of sequences, residues and the longest length of a database. */
+int hs_db_info(const hs_db *db, int64_t *n_seqs, int64_t *n_residues, int32_t *max_len);
+
+/* Releases the handle and its device memory. NULL is ignored. */
+void hs_db_free(hs_db *db);
+
+/* Device workspace needed by hs_search_device for a query length and k. */
+int hs_search_workspace_size(const hs_db *db, int32_t qlen, int32_t k, size_t *bytes);
+
+/* Ops capacity (entries) that always suffices for k hits of a query length. */
+int64_t hs_ops_capacity(int32_t qlen, int32_t k);
+
+/* The search with every buffer on the device (no host copies; asynchronous
+ * on `stream`).  Sec. III.B.3: the query d_query[qlen] (device) against every
+ * database sequence, then the top min(k, n_seqs) hits with alignments.
+ *   d_workspace : device, ws_bytes >= hs_search_workspace_size(...), 256-byte
+ *                 aligned; its contents are scratch and are overwritten.
+ *   d_hits      : device, min(k, n_seqs) records.
+ *   d_ops       : device, ops_cap entries; d_ops_used (device int64) receives
+ *                 the entries written.  If ops_cap is too small the status
+ *                 word reports HS_ETRUNC.
+ *   d_scores    : optional device int32[n_seqs], every pair's score by
+ *                 database index (NULL: not written).
+ *   d_cells     : optional device int64[n_seqs], the virtual-score cells
+ *                 (letter pairs summed) of every pair (NULL: not counted).
+ *   d_status    : device int32 receiving HS_OK or the first device-side error.
+ * Host-side argument errors are returned before anything is enqueued. */
+int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen,
+                     const hs_params *p, int32_t k, uint64_t seed, void *stream,
+                     void *d_workspace, size_t ws_bytes,
+                     hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
+                     int32_t *d_scores, int64_t *d_cells, int32_t *d_status);
+
+/* The same search from host buffers: copies the query (host, qlen codes) in,
+ * runs on `stream`, copies the hits and ops back and synchronises.
+ *   hits_out : host, room for min(k, n_seqs) records; *n_hits_out receives
+ *              the count.
+ *   ops_out  : host, ops_cap entries; *ops_used receives the entries needed;
+ *              HS_ETRUNC if ops_cap is smaller (hits are still written).
+ * Uses a device workspace cached in the handle (grown with cudaMalloc). */
+int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
+              int32_t k, uint64_t seed, void *stream,
+              hs_hit *hits_out, int32_t *n_hits_out,
+              uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used);
+
+/* One pair replayed alone (Fig. 1's AlignSequences for the query and
+ * database sequence db_index, with the same draws as hs_search): its score
+ * and its alignment ops (host buffer of `cap` entries). */
+int hs_get_alignment(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
+                     uint64_t seed, int64_t db_index, void *stream,
+                     uint32_t *ops_out, int64_t cap, int32_t *score_out,
+                     int64_t *ops_len_out, hs_hit *hit_out);
+
+/* Static message for a status code. */
+const char *hs_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSEARCH_H */

@@ -1,0 +1,216 @@
+"""GB300 heuristic protein database search (Nag & Karforma, arXiv 1508.06561).
+
+Python binding of the C ABI in ``include/hsearch.h``.  It only marshals
+arguments: every step of the search -- query profile, the pair-wise
+heuristic alignment of Fig. 1 in database mode (Sec. III.B.3), ranking and
+alignment replay -- runs in the library's CUDA kernels.  PyTorch supplies
+device memory and streams for the device-resident entry point.
+
+    db = Database(codes, offsets)               # load once (uint8 codes, int64 offsets)
+    hits, ops = search(db, query, k=10)         # host in, host out
+    out = search_device(db, q_cuda, k=10)       # torch tensors in HBM
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from ._lib import HIT_DTYPE, HS_OP_D, HS_OP_I, HS_OP_M, HsError, check, lib
+
+__all__ = ["Params", "Database", "search", "search_device", "get_alignment", "encode",
+           "builtin_matrix", "ops_to_rows", "HIT_DTYPE", "HsError", "workspace_size"]
+
+GAP = 0xFF
+
+
+@dataclass
+class Params:
+    """Sec. III.B.1 parameters; defaults are Sec. IV's (PGP=0, GOP=10, GEP=5,
+    LFactor=0.5, SFactor=1, MinFactor=0.5) with Rounds=1 (Sec. III.B.3 a).
+    Factors are Q16 fixed point (65536 == 1.0).  matrix: symmetric 24x24
+    int8 (query letter, target letter); None = built-in BLOSUM62."""
+    pgp: int = 0
+    gop: int = 10
+    gep: int = 5
+    rounds: int = 1
+    lfactor_q16: int = 32768
+    sfactor_q16: int = 65536
+    minfactor_q16: int = 32768
+    matrix: Optional[np.ndarray] = None
+
+    def to_c(self):
+        p = _lib.hs_params(self.pgp, self.gop, self.gep, self.rounds, self.lfactor_q16,
+                           self.sfactor_q16, self.minfactor_q16, _lib.HS_MODE_DB, None)
+        keep = None
+        if self.matrix is not None:
+            keep = np.ascontiguousarray(self.matrix, dtype=np.int8)
+            assert keep.shape == (24, 24)
+            p.matrix = keep.ctypes.data_as(C.POINTER(C.c_int8))
+        return p, keep
+
+
+def encode(text: str) -> np.ndarray:
+    b = text.encode("ascii")
+    out = np.zeros(len(b), np.uint8)
+    check(lib().hs_encode(b, len(b), out.ctypes.data), "hs_encode")
+    return out
+
+
+def builtin_matrix() -> np.ndarray:
+    out = np.zeros((24, 24), np.int8)
+    check(lib().hs_builtin_matrix(out.ctypes.data), "hs_builtin_matrix")
+    return out
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream   # torch.cuda.Stream
+
+
+class Database:
+    """A database resident on the current CUDA device (hs_db_load)."""
+
+    def __init__(self, codes, offsets, stream=None):
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        h = C.c_void_p()
+        check(lib().hs_db_load(codes.ctypes.data if len(codes) else None, offsets.ctypes.data,
+                               len(offsets) - 1, _stream_ptr(stream), C.byref(h)), "hs_db_load")
+        self._h = h
+        n, r, m = C.c_int64(), C.c_int64(), C.c_int32()
+        check(lib().hs_db_info(h, C.byref(n), C.byref(r), C.byref(m)), "hs_db_info")
+        self.n, self.residues, self.max_len = n.value, r.value, m.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("database closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().hs_db_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def workspace_size(db: Database, qlen: int, k: int) -> int:
+    b = C.c_size_t()
+    check(lib().hs_search_workspace_size(db.handle, qlen, k, C.byref(b)), "hs_search_workspace_size")
+    return b.value
+
+
+def search(db: Database, query, k: int, params: Params | None = None, seed: int = 0, stream=None):
+    """hs_search: host query in, (hits structured array, ops uint32 array) out."""
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    p, _keep = (params or Params()).to_c()
+    nh = min(k, db.n)
+    hits = np.zeros(max(nh, 1), HIT_DTYPE)
+    cap = lib().hs_ops_capacity(len(q), k)
+    ops = np.zeros(max(cap, 1), np.uint32)
+    n_out, used = C.c_int32(), C.c_int64()
+    check(lib().hs_search(db.handle, q.ctypes.data, len(q), C.byref(p), k, seed & (2**64 - 1),
+                          _stream_ptr(stream), hits.ctypes.data, C.byref(n_out), ops.ctypes.data,
+                          cap, C.byref(used)), "hs_search")
+    return hits[:n_out.value].copy(), ops[:used.value].copy()
+
+
+def search_device(db: Database, query, k: int, params: Params | None = None, seed: int = 0,
+                  stream=None, workspace=None, want_scores: bool = False, want_cells: bool = False,
+                  out=None):
+    """hs_search_device with torch CUDA tensors; asynchronous on `stream`.
+
+    query: uint8 CUDA tensor.  Returns a dict of CUDA tensors: hits (uint8
+    bytes, view with HIT_DTYPE after copying), ops, ops_used, status and
+    optionally scores / cells.  Pass `out` (a previous result) and
+    `workspace` to reuse buffers."""
+    import torch
+    dev = query.device
+    qlen = int(query.numel())
+    nh = min(k, db.n)
+    ws_bytes = workspace_size(db, qlen, k)
+    if workspace is None or workspace.numel() < ws_bytes:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cap = lib().hs_ops_capacity(qlen, k)
+    if out is None:
+        out = {
+            "hits": torch.empty(max(nh, 1) * HIT_DTYPE.itemsize, dtype=torch.uint8, device=dev),
+            "ops": torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+            "ops_used": torch.zeros(1, dtype=torch.int64, device=dev),
+            "status": torch.zeros(1, dtype=torch.int32, device=dev),
+        }
+        if want_scores:
+            out["scores"] = torch.empty(max(db.n, 1), dtype=torch.int32, device=dev)
+        if want_cells:
+            out["cells"] = torch.empty(max(db.n, 1), dtype=torch.int64, device=dev)
+    out["workspace"] = workspace
+    p, _keep = (params or Params()).to_c()
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    check(lib().hs_search_device(
+        db.handle, query.data_ptr(), qlen, C.byref(p), k, seed & (2**64 - 1), _stream_ptr(st),
+        workspace.data_ptr(), ws_bytes, out["hits"].data_ptr(), out["ops"].data_ptr(), cap,
+        out["ops_used"].data_ptr(),
+        out["scores"].data_ptr() if "scores" in out else None,
+        out["cells"].data_ptr() if "cells" in out else None,
+        out["status"].data_ptr()), "hs_search_device")
+    out["n_hits"] = nh
+    return out
+
+
+def device_result_to_host(out):
+    """Copies a search_device result back: (hits structured array, ops)."""
+    st = int(out["status"].item())
+    if st != 0:
+        raise HsError(st, "hs_search_device (device status)")
+    nh = out["n_hits"]
+    hits = np.frombuffer(out["hits"].cpu().numpy().tobytes(), dtype=HIT_DTYPE)[:nh].copy()
+    used = int(out["ops_used"].item()) if nh else 0
+    ops = out["ops"][:used].cpu().numpy().view(np.uint32).copy()
+    return hits, ops
+
+
+def get_alignment(db: Database, query, db_index: int, params: Params | None = None, seed: int = 0,
+                  stream=None):
+    """hs_get_alignment: (score, ops, hit record) of one pair."""
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    p, _keep = (params or Params()).to_c()
+    cap = 2 * len(q) + 4
+    ops = np.zeros(cap, np.uint32)
+    score, n = C.c_int32(), C.c_int64()
+    hit = np.zeros(1, HIT_DTYPE)
+    check(lib().hs_get_alignment(db.handle, q.ctypes.data, len(q), C.byref(p), seed & (2**64 - 1),
+                                 db_index, _stream_ptr(stream), ops.ctypes.data, cap, C.byref(score),
+                                 C.byref(n), hit.ctypes.data), "hs_get_alignment")
+    return int(score.value), ops[:n.value].copy(), hit[0]
+
+
+def ops_to_rows(ops, q, t):
+    """Expands run-length ops into the two alignment rows (GAP = 255)."""
+    rq, rt = [], []
+    i = j = 0
+    for v in np.asarray(ops, dtype=np.uint32):
+        op, n = int(v) & 3, int(v) >> 2
+        for _ in range(n):
+            if op == HS_OP_M:
+                rq.append(int(q[i])); rt.append(int(t[j])); i += 1; j += 1
+            elif op == HS_OP_I:
+                rq.append(int(q[i])); rt.append(GAP); i += 1
+            elif op == HS_OP_D:
+                rq.append(GAP); rt.append(int(t[j])); j += 1
+            else:
+                raise ValueError("bad op %d" % op)
+    if i != len(q) or j != len(t):
+        raise ValueError("ops do not cover both sequences")
+    return np.array(rq, np.uint8), np.array(rt, np.uint8)

@@ -1,0 +1,463 @@
+// hs_api.cu -- host runtime behind the C ABI of include/hsearch.h.
+// Database load (packing + length order), parameter checks, workspace
+// carve-up and the search pipeline: profile -> scan -> top-k -> replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+// BLOSUM62 (Henikoff & Henikoff, PNAS 1992), rows and columns in the order
+// A R N D C Q E G H I L K M F P S T W Y V B Z X *.
+static const int8_t kBlosum62[kNSym * kNSym] = {
+    4, -1, -2, -2, 0, -1, -1, 0, -2, -1, -1, -1, -1, -2, -1, 1, 0, -3, -2, 0, -2, -1, 0, -4,
+    -1, 5, 0, -2, -3, 1, 0, -2, 0, -3, -2, 2, -1, -3, -2, -1, -1, -3, -2, -3, -1, 0, -1, -4,
+    -2, 0, 6, 1, -3, 0, 0, 0, 1, -3, -3, 0, -2, -3, -2, 1, 0, -4, -2, -3, 3, 0, -1, -4,
+    -2, -2, 1, 6, -3, 0, 2, -1, -1, -3, -4, -1, -3, -3, -1, 0, -1, -4, -3, -3, 4, 1, -1, -4,
+    0, -3, -3, -3, 9, -3, -4, -3, -3, -1, -1, -3, -1, -2, -3, -1, -1, -2, -2, -1, -3, -3, -2, -4,
+    -1, 1, 0, 0, -3, 5, 2, -2, 0, -3, -2, 1, 0, -3, -1, 0, -1, -2, -1, -2, 0, 3, -1, -4,
+    -1, 0, 0, 2, -4, 2, 5, -2, 0, -3, -3, 1, -2, -3, -1, 0, -1, -3, -2, -2, 1, 4, -1, -4,
+    0, -2, 0, -1, -3, -2, -2, 6, -2, -4, -4, -2, -3, -3, -2, 0, -2, -2, -3, -3, -1, -2, -1, -4,
+    -2, 0, 1, -1, -3, 0, 0, -2, 8, -3, -3, -1, -2, -1, -2, -1, -2, -2, 2, -3, 0, 0, -1, -4,
+    -1, -3, -3, -3, -1, -3, -3, -4, -3, 4, 2, -3, 1, 0, -3, -2, -1, -3, -1, 3, -3, -3, -1, -4,
+    -1, -2, -3, -4, -1, -2, -3, -4, -3, 2, 4, -2, 2, 0, -3, -2, -1, -2, -1, 1, -4, -3, -1, -4,
+    -1, 2, 0, -1, -3, 1, 1, -2, -1, -3, -2, 5, -1, -3, -1, 0, -1, -3, -2, -2, 0, 1, -1, -4,
+    -1, -1, -2, -3, -1, 0, -2, -3, -2, 1, 2, -1, 5, 0, -2, -1, -1, -1, -1, 1, -3, -1, -1, -4,
+    -2, -3, -3, -3, -2, -3, -3, -3, -1, 0, 0, -3, 0, 6, -4, -2, -2, 1, 3, -1, -3, -3, -1, -4,
+    -1, -2, -2, -1, -3, -1, -1, -2, -2, -3, -3, -1, -2, -4, 7, -1, -1, -4, -3, -2, -2, -1, -2, -4,
+    1, -1, 1, 0, -1, 0, 0, 0, -1, -2, -2, 0, -1, -2, -1, 4, 1, -3, -2, -2, 0, 0, 0, -4,
+    0, -1, 0, -1, -1, -1, -1, -2, -2, -1, -1, -1, -1, -2, -1, 1, 5, -2, -2, 0, -1, -1, 0, -4,
+    -3, -3, -4, -4, -2, -2, -3, -2, -2, -3, -2, -3, -1, 1, -4, -3, -2, 11, 2, -3, -4, -3, -2, -4,
+    -2, -2, -2, -3, -2, -1, -2, -3, 2, -1, -1, -2, -1, 3, -3, -2, -2, 2, 7, -1, -3, -2, -1, -4,
+    0, -3, -3, -3, -1, -2, -2, -3, -3, 3, 1, -2, 1, -1, -2, -2, 0, -3, -1, 4, -3, -2, -1, -4,
+    -2, -1, 3, 4, -3, 0, 1, -1, 0, -3, -4, 0, -3, -3, -2, 0, -1, -4, -3, -3, 4, 1, -1, -4,
+    -1, 0, 0, 1, -3, 3, 4, -2, 0, -3, -3, 1, -1, -3, -1, 0, -1, -3, -2, -2, 1, 4, -1, -4,
+    0, -1, -1, -1, -2, -1, -1, -1, -1, -1, -1, -1, -1, -1, -2, 0, 0, -2, -1, -1, -1, -1, -1, -4,
+    -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, 1,
+};
+
+static const char kLetters[kNSym + 1] = "ARNDCQEGHILKMFPSTWYVBZX*";
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t slot_stride_for(int32_t qlen) { return 2LL * qlen + 4; }
+
+size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k)
+{
+    size_t b = 0;
+    b += align256(sizeof(uint32_t) * 2 * (size_t)profile_words(qlen));
+    b += align256(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1));
+    b += align256(sizeof(uint32_t) * kNumCounters);
+    b += align256(sizeof(uint64_t) * (size_t)kTopkCtas * std::max(k, 1));
+    b += align256(sizeof(int64_t) * (size_t)std::max(k, 1));
+    b += align256(sizeof(int32_t) * (size_t)std::max(k, 1));
+    b += align256(sizeof(uint32_t) * (size_t)std::max(k, 1) * (size_t)slot_stride_for(qlen));
+    b += align256(sizeof(int32_t) * (size_t)std::max(k, 1));
+    return b;
+}
+
+Workspace carve_workspace(void *base, int64_t n, int32_t qlen, int32_t k)
+{
+    Workspace w;
+    char *p = static_cast<char *>(base);
+    auto take = [&](size_t bytes) { char *r = p; p += align256(bytes); return r; };
+    w.prof = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 2 * (size_t)profile_words(qlen)));
+    w.scores = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+    w.counters = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * kNumCounters));
+    w.cand = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * (size_t)kTopkCtas * std::max(k, 1)));
+    w.hit_idx = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (size_t)std::max(k, 1)));
+    w.hit_score = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (size_t)std::max(k, 1)));
+    w.slot_stride = slot_stride_for(qlen);
+    w.slots = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)std::max(k, 1) * (size_t)w.slot_stride));
+    w.slot_len = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (size_t)std::max(k, 1)));
+    w.topk_ctas = kTopkCtas;
+    w.k = k;
+    return w;
+}
+
+static int from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return HS_OK;
+    if (e == cudaErrorMemoryAllocation) return HS_ENOMEM;
+    return HS_ECUDA;
+}
+
+static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams *kp)
+{
+    int rc = hs_params_check(p);
+    if (rc != HS_OK) return rc;
+    const int8_t *m = p->matrix ? p->matrix : kBlosum62;
+    int lo = 127, hi = -128;
+    for (int i = 0; i < kNSym * kNSym; i++) {
+        kp->m[i] = m[i];
+        lo = std::min<int>(lo, m[i]);
+        hi = std::max<int>(hi, m[i]);
+    }
+    kp->bias = -lo;
+    const int range = hi - lo;
+    kp->flush = range == 0 ? 255 : std::max(1, 255 / range);
+    kp->pgp = p->pgp; kp->gop = p->gop; kp->gep = p->gep; kp->rounds = p->rounds;
+    kp->lf_q16 = p->lfactor_q16; kp->sf_q16 = p->sfactor_q16; kp->minf_q16 = p->minfactor_q16;
+    kp->qlen = qlen;
+    kp->seed = seed;
+    return HS_OK;
+}
+
+}  // namespace hs
+
+using namespace hs;
+
+struct hs_db {
+    int64_t n = 0, nres = 0;
+    int32_t maxlen = 0;
+    int device = 0, num_sms = 0;
+    uint8_t *d_codes = nullptr;
+    int64_t *d_offsets = nullptr;
+    int32_t *d_order = nullptr;
+    std::vector<int32_t> sorted_len;        // lengths in scheduling order (non-increasing)
+    // host-API state (grown on demand)
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    char *d_io = nullptr;                   // query | hits | meta | ops
+    size_t io_bytes = 0;
+    char *h_io = nullptr;                   // pinned mirror of d_io
+    size_t h_io_bytes = 0;
+};
+
+extern "C" {
+
+void hs_params_default(hs_params *p)
+{
+    if (!p) return;
+    p->pgp = 0; p->gop = 10; p->gep = 5; p->rounds = 1;
+    p->lfactor_q16 = 32768; p->sfactor_q16 = 65536; p->minfactor_q16 = 32768;
+    p->mode = HS_MODE_DB;
+    p->matrix = nullptr;
+}
+
+int hs_encode(const char *ascii, int64_t n, uint8_t *codes_out)
+{
+    if (n < 0 || (n > 0 && (!ascii || !codes_out))) return HS_EINVAL;
+    uint8_t table[256];
+    for (int c = 0; c < 256; c++) table[c] = 22;   // X
+    for (int i = 0; i < kNSym; i++) {
+        table[(unsigned char)kLetters[i]] = (uint8_t)i;
+        if (kLetters[i] >= 'A' && kLetters[i] <= 'Z') table[(unsigned char)(kLetters[i] - 'A' + 'a')] = (uint8_t)i;
+    }
+    for (int64_t i = 0; i < n; i++) codes_out[i] = table[(unsigned char)ascii[i]];
+    return HS_OK;
+}
+
+int hs_builtin_matrix(int8_t *out)
+{
+    if (!out) return HS_EINVAL;
+    std::memcpy(out, kBlosum62, sizeof(kBlosum62));
+    return HS_OK;
+}
+
+int hs_params_check(const hs_params *p)
+{
+    if (!p) return HS_EINVAL;
+    if (p->pgp < 0 || p->gop < 0 || p->gep < 0) return HS_EINVAL;
+    if (p->pgp > HS_MAX_PENALTY || p->gop > HS_MAX_PENALTY || p->gep > HS_MAX_PENALTY) return HS_EINVAL;
+    if (p->rounds < 1 || p->rounds > 1000) return HS_EINVAL;
+    if (p->lfactor_q16 > 65536 || p->sfactor_q16 > 65536 || p->minfactor_q16 > 65536) return HS_EINVAL;
+    if (p->mode != HS_MODE_DB) return HS_EINVAL;
+    if (p->matrix) {
+        for (int a = 0; a < kNSym; a++)
+            for (int b = 0; b < a; b++)
+                if (p->matrix[a * kNSym + b] != p->matrix[b * kNSym + a]) return HS_EINVAL;
+    }
+    return HS_OK;
+}
+
+const char *hs_strerror(int status)
+{
+    switch (status) {
+    case HS_OK: return "ok";
+    case HS_EINVAL: return "invalid argument";
+    case HS_ENOMEM: return "out of memory";
+    case HS_ECUDA: return "CUDA error";
+    case HS_ETOOLONG: return "sequence or query too long";
+    case HS_ETIMEOUT: return "device wait timed out";
+    case HS_ETRUNC: return "output buffer too small";
+    case HS_EINTERNAL: return "internal error: replay disagrees with scan";
+    default: return "unknown status";
+    }
+}
+
+void hs_db_free(hs_db *db)
+{
+    if (!db) return;
+    cudaFree(db->d_codes);
+    cudaFree(db->d_offsets);
+    cudaFree(db->d_order);
+    cudaFree(db->d_ws);
+    cudaFree(db->d_io);
+    if (db->h_io) cudaFreeHost(db->h_io);
+    delete db;
+}
+
+int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, void *stream, hs_db **out)
+{
+    if (!out || !offsets || n_seqs < 0 || n_seqs > INT32_MAX - 1) return HS_EINVAL;
+    *out = nullptr;
+    if (offsets[0] != 0) return HS_EINVAL;
+    int32_t maxlen = 0;
+    for (int64_t i = 0; i < n_seqs; i++) {
+        const int64_t len = offsets[i + 1] - offsets[i];
+        if (len < 0) return HS_EINVAL;
+        if (len > HS_MAX_SEQ_LEN) return HS_ETOOLONG;
+        maxlen = std::max<int32_t>(maxlen, (int32_t)len);
+    }
+    const int64_t nres = offsets[n_seqs];
+    if (nres > 0 && !codes) return HS_EINVAL;
+    for (int64_t i = 0; i < nres; i++)
+        if (codes[i] >= kNSym) return HS_EINVAL;
+
+    hs_db *db = new (std::nothrow) hs_db();
+    if (!db) return HS_ENOMEM;
+    db->n = n_seqs;
+    db->nres = nres;
+    db->maxlen = maxlen;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&db->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->device);
+    if (e != cudaSuccess) { hs_db_free(db); return from_cuda(e); }
+
+    // scheduling order: longest first, ties by index (results never depend on it)
+    std::vector<int32_t> order((size_t)n_seqs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+    });
+    db->sorted_len.resize((size_t)n_seqs);
+    for (int64_t i = 0; i < n_seqs; i++) db->sorted_len[i] = (int32_t)(offsets[order[i] + 1] - offsets[order[i]]);
+
+    e = cudaMalloc(&db->d_codes, (size_t)nres + kCodesPad);
+    if (e == cudaSuccess) e = cudaMalloc(&db->d_offsets, sizeof(int64_t) * (size_t)(n_seqs + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&db->d_order, sizeof(int32_t) * (size_t)std::max<int64_t>(n_seqs, 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(db->d_codes + nres, 0, kCodesPad, st);
+    if (e == cudaSuccess && nres > 0) e = cudaMemcpyAsync(db->d_codes, codes, (size_t)nres, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_offsets, offsets, sizeof(int64_t) * (size_t)(n_seqs + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_seqs > 0) e = cudaMemcpyAsync(db->d_order, order.data(), sizeof(int32_t) * (size_t)n_seqs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { hs_db_free(db); return from_cuda(e); }
+    *out = db;
+    return HS_OK;
+}
+
+int hs_db_info(const hs_db *db, int64_t *n_seqs, int64_t *n_residues, int32_t *max_len)
+{
+    if (!db) return HS_EINVAL;
+    if (n_seqs) *n_seqs = db->n;
+    if (n_residues) *n_residues = db->nres;
+    if (max_len) *max_len = db->maxlen;
+    return HS_OK;
+}
+
+int hs_search_workspace_size(const hs_db *db, int32_t qlen, int32_t k, size_t *bytes)
+{
+    if (!db || !bytes || qlen < 1 || k < 0) return HS_EINVAL;
+    if (qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    if (k > HS_MAX_K) return HS_EINVAL;
+    *bytes = workspace_bytes(db->n, qlen, k);
+    return HS_OK;
+}
+
+int64_t hs_ops_capacity(int32_t qlen, int32_t k)
+{
+    if (qlen < 1 || k < 0) return 0;
+    return (int64_t)k * slot_stride_for(qlen);
+}
+
+int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, const hs_params *p, int32_t k,
+                     uint64_t seed, void *stream, void *d_workspace, size_t ws_bytes, hs_hit *d_hits,
+                     uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used, int32_t *d_scores,
+                     int64_t *d_cells, int32_t *d_status)
+{
+    if (!db || !d_query || !p || !d_workspace || !d_status) return HS_EINVAL;
+    if (qlen < 1) return HS_EINVAL;
+    if (qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    if (k < 0 || k > HS_MAX_K || ops_cap < 0) return HS_EINVAL;
+    const int32_t nhits = (int32_t)std::min<int64_t>(k, db->n);
+    if (nhits > 0 && (!d_hits || !d_ops_used || (ops_cap > 0 && !d_ops))) return HS_EINVAL;
+    if (((uintptr_t)d_workspace & 255) != 0) return HS_EINVAL;
+    if (ws_bytes < workspace_bytes(db->n, qlen, k)) return HS_ETRUNC;
+    KParams kp;
+    int rc = make_kparams(p, qlen, seed, &kp);
+    if (rc != HS_OK) return rc;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Workspace ws = carve_workspace(d_workspace, db->n, qlen, k);
+    if (d_scores) ws.scores = d_scores;
+    cudaError_t e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * kNumCounters, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (nhits == 0 && d_ops_used) {
+        e = cudaMemsetAsync(d_ops_used, 0, sizeof(int64_t), st);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (db->n == 0) return HS_OK;
+
+    // role split and the long prefix in the length order
+    const auto &L = db->sorted_len;
+    const int64_t split = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= qlen; }) - L.begin();
+    const int64_t long_end = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
+    DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
+    e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st);
+    if (e == cudaSuccess && nhits > 0) e = launch_topk(ws, db->n, nhits, st);
+    if (e == cudaSuccess && nhits > 0)
+        e = launch_replay(v, d_query, kp, ws, nhits, d_hits, d_ops, ops_cap, d_ops_used, d_status, st);
+    return from_cuda(e);
+}
+
+// host-API buffers: [query | hits | ops_used, status | ops]
+struct IoLayout {
+    size_t q, hits, meta, ops, total;
+};
+static IoLayout io_layout(int32_t qlen, int32_t k)
+{
+    IoLayout l;
+    l.q = 0;
+    l.hits = align256((size_t)qlen);
+    l.meta = l.hits + align256(sizeof(hs_hit) * (size_t)std::max(k, 1));
+    l.ops = l.meta + 256;
+    l.total = l.ops + align256(sizeof(uint32_t) * (size_t)std::max<int64_t>(hs_ops_capacity(qlen, k), 1));
+    return l;
+}
+
+static int ensure_host_state(hs_db *db, size_t ws_need, size_t io_need)
+{
+    cudaError_t e = cudaSuccess;
+    if (db->ws_bytes < ws_need) {
+        cudaFree(db->d_ws);
+        db->d_ws = nullptr;
+        db->ws_bytes = 0;
+        e = cudaMalloc(&db->d_ws, ws_need);
+        if (e != cudaSuccess) return from_cuda(e);
+        db->ws_bytes = ws_need;
+    }
+    if (db->io_bytes < io_need) {
+        cudaFree(db->d_io);
+        db->d_io = nullptr;
+        db->io_bytes = 0;
+        e = cudaMalloc(&db->d_io, io_need);
+        if (e != cudaSuccess) return from_cuda(e);
+        db->io_bytes = io_need;
+    }
+    if (db->h_io_bytes < io_need) {
+        if (db->h_io) cudaFreeHost(db->h_io);
+        db->h_io = nullptr;
+        db->h_io_bytes = 0;
+        e = cudaMallocHost(&db->h_io, io_need);
+        if (e != cudaSuccess) return from_cuda(e);
+        db->h_io_bytes = io_need;
+    }
+    return HS_OK;
+}
+
+int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p, int32_t k, uint64_t seed,
+              void *stream, hs_hit *hits_out, int32_t *n_hits_out, uint32_t *ops_out, int64_t ops_cap,
+              int64_t *ops_used)
+{
+    if (!db || !query || !p || !n_hits_out || !ops_used) return HS_EINVAL;
+    if (qlen < 1) return HS_EINVAL;
+    if (qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    if (k < 0 || k > HS_MAX_K || ops_cap < 0) return HS_EINVAL;
+    const int32_t nhits = (int32_t)std::min<int64_t>(k, db->n);
+    if (nhits > 0 && !hits_out) return HS_EINVAL;
+    for (int32_t i = 0; i < qlen; i++)
+        if (query[i] >= kNSym) return HS_EINVAL;
+    int rc = hs_params_check(p);
+    if (rc != HS_OK) return rc;
+    const IoLayout l = io_layout(qlen, k);
+    rc = ensure_host_state(db, workspace_bytes(db->n, qlen, k), l.total);
+    if (rc != HS_OK) return rc;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *h = db->h_io, *d = db->d_io;
+    std::memcpy(h + l.q, query, (size_t)qlen);
+    cudaError_t e = cudaMemcpyAsync(d + l.q, h + l.q, (size_t)qlen, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    const int64_t cap = hs_ops_capacity(qlen, k);
+    rc = hs_search_device(db, reinterpret_cast<const uint8_t *>(d + l.q), qlen, p, k, seed, stream, db->d_ws,
+                          db->ws_bytes, reinterpret_cast<hs_hit *>(d + l.hits), reinterpret_cast<uint32_t *>(d + l.ops),
+                          cap, reinterpret_cast<int64_t *>(d + l.meta), nullptr, nullptr,
+                          reinterpret_cast<int32_t *>(d + l.meta + 8));
+    if (rc != HS_OK) return rc;
+    // one copy back: hits, ops_used/status and the packed ops
+    e = cudaMemcpyAsync(h + l.hits, d + l.hits, l.total - l.hits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    int64_t used;
+    int32_t status;
+    std::memcpy(&used, h + l.meta, sizeof(used));
+    std::memcpy(&status, h + l.meta + 8, sizeof(status));
+    if (nhits == 0) used = 0;
+    if (status != HS_OK) return status;
+    if (nhits > 0) std::memcpy(hits_out, h + l.hits, sizeof(hs_hit) * (size_t)nhits);
+    *n_hits_out = nhits;
+    *ops_used = used;
+    if (used > ops_cap) return HS_ETRUNC;
+    if (used > 0) std::memcpy(ops_out, h + l.ops, sizeof(uint32_t) * (size_t)used);
+    return HS_OK;
+}
+
+int hs_get_alignment(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p, uint64_t seed,
+                     int64_t db_index, void *stream, uint32_t *ops_out, int64_t cap, int32_t *score_out,
+                     int64_t *ops_len_out, hs_hit *hit_out)
+{
+    if (!db || !query || !p || cap < 0 || (cap > 0 && !ops_out)) return HS_EINVAL;
+    if (qlen < 1) return HS_EINVAL;
+    if (qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    if (db_index < 0 || db_index >= db->n) return HS_EINVAL;
+    for (int32_t i = 0; i < qlen; i++)
+        if (query[i] >= kNSym) return HS_EINVAL;
+    KParams kp;
+    int rc = make_kparams(p, qlen, seed, &kp);
+    if (rc != HS_OK) return rc;
+    // ops of one pair: at most 2 per step plus the tail
+    const int64_t need = slot_stride_for(qlen);
+    IoLayout l = io_layout(qlen, 1);
+    l.total = std::max(l.total, l.ops + align256(sizeof(uint32_t) * (size_t)need));
+    rc = ensure_host_state(db, workspace_bytes(db->n, qlen, 1), l.total);
+    if (rc != HS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *h = db->h_io, *d = db->d_io;
+    std::memcpy(h + l.q, query, (size_t)qlen);
+    cudaError_t e = cudaMemcpyAsync(d + l.q, h + l.q, (size_t)qlen, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + l.meta, 0, 16, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    Workspace ws = carve_workspace(db->d_ws, db->n, qlen, 1);
+    DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
+    e = launch_replay_one(v, reinterpret_cast<const uint8_t *>(d + l.q), kp, ws, db_index,
+                          reinterpret_cast<uint32_t *>(d + l.ops), need, reinterpret_cast<hs_hit *>(d + l.hits),
+                          reinterpret_cast<int64_t *>(d + l.meta), reinterpret_cast<int32_t *>(d + l.meta + 8), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + l.hits, d + l.hits, l.total - l.hits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    int64_t used;
+    int32_t status;
+    std::memcpy(&used, h + l.meta, sizeof(used));
+    std::memcpy(&status, h + l.meta + 8, sizeof(status));
+    if (status != HS_OK && status != HS_ETRUNC) return status;
+    hs_hit hit;
+    std::memcpy(&hit, h + l.hits, sizeof(hit));
+    if (score_out) *score_out = hit.score;
+    if (ops_len_out) *ops_len_out = used;
+    if (hit_out) *hit_out = hit;
+    if (used > cap) return HS_ETRUNC;
+    if (used > 0) std::memcpy(ops_out, h + l.ops, sizeof(uint32_t) * (size_t)used);
+    return HS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// hs_internal.h -- declarations shared by the library's translation units
+// (host runtime <-> kernels).  Not part of the public C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hsearch.h"
+
+namespace hs {
+
+constexpr int kNSym = 24;               // BLOSUM62 alphabet (Sec. III.A)
+constexpr int kWarpsPerCta = 8;         // scan kernel: 256 threads
+constexpr int kTopkThreads = 512;
+constexpr int kLongLen = 2048;          // targets this long are scheduled one per warp
+constexpr int kShortChunk = 8;          // shorter targets are taken 8 at a time
+constexpr int kCodesPad = 64;           // readable bytes past the last residue
+
+// Query profile geometry: 4 byte-shifted copies x 24 letters x S words,
+// S odd (so the 24 rows of a column sit in distinct shared-memory banks) and
+// wide enough for 4 zero columns before and 12 after the query.
+__host__ __device__ inline int profile_stride(int qlen) { return ((qlen + 16) >> 2) | 1; }
+__host__ __device__ inline int64_t profile_words(int qlen) { return 4LL * kNSym * profile_stride(qlen); }
+
+// Everything a kernel needs to score pairs; passed by value as a kernel
+// argument, so launching needs no host->device copy of the parameters.
+struct KParams {
+    int8_t m[kNSym * kNSym];            // M[query letter][target letter]
+    int32_t bias;                       // -min(M): M + bias >= 0
+    int32_t flush;                      // byte-lane flush interval: floor(255 / (max-min))
+    int32_t pgp, gop, gep, rounds;
+    uint32_t lf_q16, sf_q16, minf_q16;  // LFactor, SFactor, MinFactor in Q16
+    int32_t qlen;
+    uint64_t seed;
+};
+
+// Device view of a loaded database.
+struct DbView {
+    const uint8_t *codes;               // residues, kCodesPad readable bytes past the end
+    const int64_t *offsets;             // n + 1
+    const int32_t *order;               // database indices, longest first
+    int64_t n;
+};
+
+// Workspace carve-up (all offsets 256-byte aligned).
+struct Workspace {
+    uint32_t *prof;                     // [2 * profile words] reversed, then forward query profile
+    int32_t *scores;                    // [n] by database index
+    uint32_t *counters;                 // [kNumCounters], zeroed per search
+    uint64_t *cand;                     // [topk_ctas * k] per-CTA top-k keys
+    int64_t *hit_idx;                   // [k] database index of each ranked hit
+    int32_t *hit_score;                 // [k]
+    uint32_t *slots;                    // [k * slot_stride] replayed ops
+    int32_t *slot_len;                  // [k]
+    int64_t slot_stride;
+    int32_t topk_ctas;
+    int32_t k;
+};
+enum Counter { kQsLong = 0, kQsShort = 1, kQlLong = 2, kQlShort = 3, kTopkTicket = 4, kReplayTicket = 5,
+               kNumCounters = 8 };
+
+constexpr int kTopkCtas = 152;
+
+size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k);
+Workspace carve_workspace(void *base, int64_t n, int32_t qlen, int32_t k);
+int64_t slot_stride_for(int32_t qlen);
+
+// Launchers (hs_scan.cu / hs_topk.cu).  Return a cudaError_t.
+// Role split: targets at sorted positions [0, split) are at least as long
+// as the query (the query is the small sequence); [split, n) are shorter.
+// long_end: sorted positions [0, long_end) hold targets of >= kLongLen letters.
+cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
+                        const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
+                        cudaStream_t st);
+size_t scan_smem_bytes(int32_t qlen);
+cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st);
+cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParams &kp,
+                          const Workspace &ws, int32_t nhits, hs_hit *d_hits, uint32_t *d_ops,
+                          int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st);
+cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KParams &kp,
+                              const Workspace &ws, int64_t db_index, uint32_t *d_ops, int64_t cap,
+                              hs_hit *d_hit, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st);
+
+}  // namespace hs

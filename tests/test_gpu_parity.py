@@ -1,0 +1,215 @@
+"""GPU path vs the CPU oracle, bit for bit (all arithmetic is integer).
+
+Every test calls the library through its C ABI (via the ctypes binding) and
+compares with ``oracle`` on the same seeded inputs: every pair's score and
+cell count, the ranked hits, and every hit's alignment rows.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1508_06561_gb300 as P
+from paper_1508_06561_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_06561_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+
+
+def oparams(p: P.Params):
+    return O.paper_params(pgp=p.pgp, gop=p.gop, gep=p.gep, rounds=p.rounds, lfactor_q16=p.lfactor_q16,
+                          sfactor_q16=p.sfactor_q16, minfactor_q16=p.minfactor_q16)
+
+
+def run_device(D, q, k, params, seed):
+    qd = torch.from_numpy(np.ascontiguousarray(q, np.uint8)).cuda()
+    out = P.search_device(D, qd, k, params, seed=seed, want_scores=True, want_cells=True)
+    torch.cuda.synchronize()
+    hits, ops = P.device_result_to_host(out)
+    scores = out["scores"].cpu().numpy()[: D.n].astype(np.int64)
+    cells = out["cells"].cpu().numpy()[: D.n]
+    return hits, ops, scores, cells
+
+
+def check_hits(db, q, M, op, seed, hits, ops, ref_scores, k):
+    want = O.topk(ref_scores, k)
+    assert hits["db_index"].tolist() == want.tolist()
+    assert hits["score"].tolist() == ref_scores[want].tolist()
+    for h in hits:
+        t = db.seq(int(h["db_index"]))
+        seg = ops[h["ops_offset"]:h["ops_offset"] + h["ops_len"]]
+        rq, rt = P.ops_to_rows(seg, q, t)
+        s, oq, ot, _, _ = O.align_pair(q, t, M, op, seed, int(h["db_index"]))
+        assert s == h["score"]
+        assert np.array_equal(rq, oq) and np.array_equal(rt, ot)
+        assert O.score_rows(rq, rt, M, op.pgp, op.gop, op.gep) == h["score"]
+        m = (rq != 255) & (rt != 255)
+        if m.any():
+            cols = np.nonzero(m)[0]
+            qpos = np.cumsum(rq != 255) - 1
+            tpos = np.cumsum(rt != 255) - 1
+            assert (h["q_begin"], h["q_end"]) == (qpos[cols[0]], qpos[cols[-1]] + 1)
+            assert (h["t_begin"], h["t_end"]) == (tpos[cols[0]], tpos[cols[-1]] + 1)
+
+
+def full_parity(db, q, k, params, seed, M=None):
+    M = O.blosum62() if params.matrix is None else params.matrix
+    op = oparams(params)
+    D = P.Database(db.codes, db.offsets)
+    hits, ops, scores, cells = run_device(D, q, k, params, seed)
+    ref, ref_cells, _ = O.search_scores(db.codes, db.offsets, q, M, op, seed)
+    bad = np.nonzero(scores != ref)[0]
+    assert len(bad) == 0, "score mismatch at %s: gpu %s oracle %s" % (bad[:5], scores[bad[:5]], ref[bad[:5]])
+    assert np.array_equal(cells, ref_cells)
+    check_hits(db, q, M, op, seed, hits, ops, ref, min(k, db.n))
+    # the host-buffer entry point returns the same hits and ops
+    h2, o2 = P.search(D, q, k, params, seed)
+    assert np.array_equal(h2, hits) and np.array_equal(o2, ops)
+    D.close()
+    return scores
+
+
+def test_plain_small_workload():
+    db, q, k = synth.plain_small(0)
+    full_parity(db, q, k, P.Params(), seed=0)
+
+
+EDGE_QLENS = [1, 2, 3, 4, 5, 7, 31, 64, 127, 255, 256, 257, 600]
+
+
+@pytest.mark.parametrize("case", range(len(EDGE_QLENS)))
+def test_random_databases(case):
+    rng = np.random.default_rng(9000 + case)
+    qlen = EDGE_QLENS[case]
+    n = int(rng.integers(1, 400))
+    lengths = np.concatenate([
+        rng.integers(0, 4, n // 8 + 1),                       # empty and tiny targets
+        rng.integers(max(1, qlen - 3), qlen + 4, n // 8 + 1),  # around the role switch
+        synth.lognormal_lengths(rng, n, 250, 0.8, 1, 3000),
+    ])
+    rng.shuffle(lengths)
+    db = synth.db_from_lengths(rng, lengths)
+    q = synth.residues(rng, qlen)
+    kind = case % 4
+    if kind == 0:
+        params = P.Params()
+    elif kind == 1:
+        params = P.Params(pgp=int(rng.integers(0, 4)), gop=int(rng.integers(0, 20)), gep=int(rng.integers(0, 7)),
+                          rounds=int(rng.integers(1, 4)), lfactor_q16=int(rng.integers(1, 65537)),
+                          sfactor_q16=int(rng.integers(1, 65537)), minfactor_q16=int(rng.integers(0, 65537)))
+    elif kind == 2:   # a wide matrix: flush every 3 cells
+        params = P.Params(matrix=synth.random_symmetric_matrix(rng, -40, 50), rounds=2)
+    else:             # the widest int8 range: flush every cell
+        params = P.Params(matrix=synth.random_symmetric_matrix(rng, -128, 127), pgp=1)
+    full_parity(db, q, int(rng.integers(1, 40)), params, seed=int(rng.integers(0, 2**63)))
+
+
+def test_paper_example_factor_setting():
+    """Sec. III.B.1's suggested setting (SFactor=0.5 < LFactor=1)."""
+    rng = np.random.default_rng(77)
+    db = synth.db_from_lengths(rng, synth.lognormal_lengths(rng, 300, 300, 0.6, 1, 2000))
+    q = synth.residues(rng, 120)
+    full_parity(db, q, 20, P.Params(lfactor_q16=65536, sfactor_q16=32768), seed=5)
+
+
+def test_long_targets_and_long_query():
+    rng = np.random.default_rng(31)
+    lengths = np.array([35_000, 20_000, 9000, 5000, 2048, 2047, 2100, 1999, 300, 17, 0, 1] + [400] * 30)
+    db = synth.db_from_lengths(rng, lengths)
+    for qlen in [2048, 1500, 64]:
+        q = synth.residues(rng, qlen)
+        full_parity(db, q, 10, P.Params(), seed=qlen)
+
+
+def test_k_edge_cases():
+    rng = np.random.default_rng(5)
+    db = synth.db_from_lengths(rng, [50, 0, 120, 7])
+    q = synth.residues(rng, 30)
+    D = P.Database(db.codes, db.offsets)
+    hits, ops = P.search(D, q, 0)
+    assert len(hits) == 0 and len(ops) == 0
+    hits, ops = P.search(D, q, 100)            # k > n: every target, ranked
+    ref, _, _ = O.search_scores(db.codes, db.offsets, q, O.blosum62(), O.paper_params(), 0)
+    assert hits["db_index"].tolist() == O.topk(ref, 4).tolist()
+    D.close()
+    one = synth.db_from_lengths(rng, [0])
+    D1 = P.Database(one.codes, one.offsets)
+    hits, ops = P.search(D1, q, 3)
+    assert len(hits) == 1 and hits[0]["score"] == 0 and hits[0]["q_begin"] == -1
+    assert P.ops_to_rows(ops, q, one.seq(0))[1].tolist() == [255] * 30
+    D1.close()
+
+
+def test_get_alignment_matches_search():
+    rng = np.random.default_rng(12)
+    db = synth.db_from_lengths(rng, synth.lognormal_lengths(rng, 200, 300, 0.6, 1, 2000))
+    q = synth.residues(rng, 90)
+    D = P.Database(db.codes, db.offsets)
+    params = P.Params(pgp=2, rounds=3, lfactor_q16=50000)
+    hits, ops = P.search(D, q, 8, params, seed=44)
+    for h in hits:
+        s, o, rec = P.get_alignment(D, q, int(h["db_index"]), params, seed=44)
+        assert s == h["score"]
+        assert o.tolist() == ops[h["ops_offset"]:h["ops_offset"] + h["ops_len"]].tolist()
+    # any pair, not only hits
+    for d in [0, 1, 57, 199]:
+        s, o, _ = P.get_alignment(D, q, d, params, seed=44)
+        ref = O.align_pair(q, db.seq(d), O.blosum62(), oparams(params), 44, d)
+        assert s == ref[0]
+        rq, rt = P.ops_to_rows(o, q, db.seq(d))
+        assert np.array_equal(rq, ref[1]) and np.array_equal(rt, ref[2])
+    D.close()
+
+
+def test_repeatable_across_runs_and_streams():
+    rng = np.random.default_rng(3)
+    db = synth.db_from_lengths(rng, synth.lognormal_lengths(rng, 1000, 300, 0.6, 1, 4000))
+    q = synth.residues(rng, 100)
+    D = P.Database(db.codes, db.offsets)
+    a = P.search(D, q, 50, seed=8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = P.search(D, q, 50, seed=8, stream=s)
+    c = P.search(D, q, 50, seed=9)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert not np.array_equal(a[0]["score"], c[0]["score"]) or not np.array_equal(a[1], c[1])
+    D.close()
+
+
+def test_swissprot_scale_sampled():
+    """The plain database-scale workload (256-residue query, ~570k targets,
+    ~205M residues, top-100) in the benchmark's launch configuration:
+    oracle scores on a random sample plus every hit, the ranking checked
+    against the GPU's own full score array, every hit's alignment checked."""
+    db, q, k = synth.plain_large()
+    D = P.Database(db.codes, db.offsets)
+    params = P.Params()
+    qd = torch.from_numpy(q).cuda()
+    out = P.search_device(D, qd, k, params, seed=1, want_scores=True)
+    torch.cuda.synchronize()
+    hits, ops = P.device_result_to_host(out)
+    scores = out["scores"].cpu().numpy()[: D.n].astype(np.int64)
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([rng.choice(db.n, 3000, replace=False), hits["db_index"],
+                                       np.argsort(-db.lengths())[:20]]))
+    ref, _, _ = O.search_scores(db.codes, db.offsets, q, O.blosum62(), O.paper_params(), 1, idx=sample)
+    assert np.array_equal(scores[sample], ref)
+    want = np.lexsort((np.arange(db.n), -scores))[:k]
+    assert hits["db_index"].tolist() == want.tolist()
+    M, op = O.blosum62(), O.paper_params()
+    for h in hits:
+        t = db.seq(int(h["db_index"]))
+        rq, rt = P.ops_to_rows(ops[h["ops_offset"]:h["ops_offset"] + h["ops_len"]], q, t)
+        s, oq, ot, _, _ = O.align_pair(q, t, M, op, 1, int(h["db_index"]))
+        assert s == h["score"] and np.array_equal(rq, oq) and np.array_equal(rt, ot)
+    D.close()
