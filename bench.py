@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the plain database search (one query against the whole
+database, Sec. III.B.3 / Sec. IV of the paper) on the GPU.
+
+A step is one complete search with the database resident in HBM: query
+profile, the scan of every pair, top-k ranking and alignment replay of the
+hits.  Default workload: a 256-residue query against a synthetic
+SwissProt-like database (~570k sequences, ~205M residues, lognormal lengths
+with median 300 and a tail to 35,000), top-100, the paper's parameters.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is database residues/s with the
+query already on the device; `e2e` is the same metric through the
+host-buffer C-ABI call (query copied in, hits and alignments copied out,
+every step).  `--impl reference` times the CPU oracle (the plain C
+implementation of the paper's algorithm) on the host cores instead.
+Multi-GPU (torchrun): every rank searches its own database shard of the
+same size (weak scaling); ranks exchange only the step time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DB residues/s per query (plain vs batched); p50/p99 query latency in serving mode"
+UNIT = "residues/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain-large", choices=["plain-large", "plain-small"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0,
+                    help="wall-time budget of the oracle CPU baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(name, rank):
+    from paper_1508_06561_gb300 import synth
+    if name == "plain-small":
+        db, q, k = synth.plain_small(0)
+        wl = "plain-q64-2k"
+    else:
+        db, q, k = synth.plain_large(seed_db=2 + rank)
+        wl = "plain-q256-swissprot-like-570k"
+    cfg = {"workload": wl, "n_seqs": int(db.n), "residues": int(db.residues), "qlen": int(len(q)), "k": int(k),
+           "params": "PGP=0 GOP=10 GEP=5 LFactor=0.5 SFactor=1 MinFactor=0.5 Rounds=1 BLOSUM62",
+           "queries_per_step": 1,
+           "l2": ("no flush: the %.0f MB residue stream exceeds the 129 MB L2" % (db.residues / 1e6)
+                  if db.residues > 129e6 else "database fits in L2; steps run warm")}
+    return db, q, k, cfg
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = (uuid or "").lower().replace("gpu-", "")
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, n = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0].lower():
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            n += 1
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+# --------------------------------------------------------------------------
+# ncu traffic recorded in profiles/ (valid only for the same kernel source)
+# --------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ["hs_device.cuh", "hs_scan.cu", "hs_internal.h"]:
+        h.update(open(os.path.join(ROOT, "paper_1508_06561_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name):
+    path = os.path.join(ROOT, "profiles", "scan_kernel_%s.md" % workload_name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline field)
+# --------------------------------------------------------------------------
+def oracle_rate(db, q, seed, budget_s, rng_seed=0, first=2000):
+    """Oracle residues/s on a growing random sample of the database, stopping
+    once `budget_s` of wall time is spent (or the database is exhausted)."""
+    import oracle as O
+    O.build()
+    M, p = O.blosum62(), O.paper_params()
+    order = np.random.default_rng(rng_seed).permutation(db.n)
+    lens = db.lengths()
+    done, res, t_used, chunk = 0, 0, 0.0, first
+    threads = os.cpu_count() or 1
+    while done < db.n and t_used < budget_s:
+        idx = np.sort(order[done:done + chunk])
+        t0 = time.perf_counter()
+        _, _, used = O.search_scores(db.codes, db.offsets, q, M, p, seed, idx=idx, nthreads=threads, want_cells=False)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        res += int(lens[idx].sum())
+        done += len(idx)
+        rate = res / max(t_used, 1e-9)
+        chunk = int(min(max(chunk, rate * min(2.0, budget_s - t_used) / max(lens.mean(), 1)), db.n - done)) or 1
+        threads = used
+    return res / t_used, threads, done, res, t_used
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    db, q, k, cfg = workload(args.workload, 0)
+    import oracle as O
+    O.build()
+    M, p = O.blosum62(), O.paper_params()
+    lens = db.lengths()
+    threads = os.cpu_count() or 1
+    # per-step sample sized so the whole run takes about two minutes
+    rate, threads, _, _, _ = oracle_rate(db, q, args.seed, 1.0, rng_seed=99, first=2000)
+    per_step_s = max(0.02, 120.0 / max(1, args.steps + args.warmup))
+    n_per_step = int(max(50, min(db.n, per_step_s * rate / max(lens.mean(), 1))))
+    rng = np.random.default_rng(12345)
+    total_res, total_t = 0, 0.0
+    for step in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(db.n, n_per_step, replace=False))
+        t0 = time.perf_counter()
+        _, _, used = O.search_scores(db.codes, db.offsets, q, M, p, args.seed, idx=idx, nthreads=threads,
+                                     want_cells=False)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            total_t += dt
+            total_res += int(lens[idx].sum())
+    value = total_res / total_t
+    sample = ("each step: %d random sequences (%.1f%% of the %d-sequence database), scores only, "
+              "%d host threads" % (n_per_step, 100.0 * n_per_step / db.n, db.n, used))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import ctypes as C
+
+    import torch
+
+    import paper_1508_06561_gb300 as P
+    from paper_1508_06561_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    P.build.build()
+    L = _lib.lib()
+
+    db, q, k, cfg = workload(args.workload, rank)
+    D = P.Database(db.codes, db.offsets)
+    params = P.Params()
+    stream = torch.cuda.Stream(dev)
+    qd = torch.from_numpy(q).to(dev)
+
+    # one untimed search counts the algorithmic cells (the scan's work)
+    with torch.cuda.stream(stream):
+        out = P.search_device(D, qd, k, params, seed=args.seed, stream=stream, want_cells=True)
+    stream.synchronize()
+    cells_per_search = int(out["cells"][: D.n].sum().item())
+    assert int(out["status"].item()) == 0
+    out = P.search_device(D, qd, k, params, seed=args.seed, stream=stream)   # buffers without counters
+    ws = out["workspace"]
+
+    # trace hook: events around the scan kernel of every timed step
+    tr = _lib.hs_trace()
+    L.hs_db_set_trace(D.handle, C.byref(tr))
+
+    def step(ev_pair=None):
+        if ev_pair is not None:
+            tr.scan_start = ev_pair[0].cuda_event
+            tr.scan_stop = ev_pair[1].cuda_event
+        else:
+            tr.scan_start = tr.scan_stop = None
+        P.search_device(D, qd, k, params, seed=args.seed, stream=stream, workspace=ws, out=out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    stream.synchronize()
+    launches_per_step = int(tr.launches)
+
+    scan_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+    for a, b in scan_events:          # torch creates events on first record
+        a.record(stream)
+        b.record(stream)
+    stream.synchronize()
+    t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.4)
+    with torch.cuda.stream(stream):
+        t_begin.record(stream)
+        for i in range(args.steps):
+            step(scan_events[i])
+        t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        torch.distributed.barrier()
+    assert int(out["status"].item()) == 0
+    ms_total = t_begin.elapsed_time(t_end)
+    scan_ms = [a.elapsed_time(b) for a, b in scan_events]
+    L.hs_db_set_trace(D.handle, None)
+
+    t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * db.residues * args.steps / (ms_max / 1000.0)
+
+    # end to end: the host-buffer call a user makes (query H2D, hits+ops D2H)
+    h2d, d2h = C.c_int64(), C.c_int64()
+    L.hs_search_transfer_bytes(len(q), k, C.byref(h2d), C.byref(d2h))
+    n_e2e = max(3, min(args.steps, 500))
+    for _ in range(3):
+        P.search(D, q, k, params, seed=args.seed, stream=stream)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        hits, ops = P.search(D, q, k, params, seed=args.seed, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * db.residues * n_e2e / float(te.item())
+
+    if rank != 0:
+        D.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the scan kernel: algorithmic cells per launch / its event time
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    scan_s = float(np.mean(scan_ms)) / 1000.0
+    achieved = cells_per_search / scan_s / 1e12
+    peak = sms * 128 * 4 * 2070e6 / 1e12     # INT32 lanes x 4 byte lanes x max SM clock
+    traffic = recorded_traffic(cfg["workload"])
+
+    cpu_rate, cpu_threads, ns, nres, tcpu = oracle_rate(db, q, args.seed, args.cpu_budget_s) \
+        if world == 1 else (None, None, 0, 0, 0.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d.value),
+                "d2h_bytes_per_step": int(d2h.value), "steps": n_e2e},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcell/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "scan_kernel", "scan_ms": scan_s * 1000.0,
+                     "cells_per_launch": cells_per_search,
+                     "peak_basis": "%d SMs x 128 INT32 lanes x 4 byte-lane cells x 2070 MHz (derived)" % sms},
+        "clocks": clk,
+    }
+    if cpu_rate is not None:
+        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+                                "sample": "%d random sequences (%d residues) of the same database, scores only, "
+                                          "%.1f s" % (ns, nres, tcpu)}
+    D.close()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

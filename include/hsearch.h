@@ -104,9 +104,9 @@ int hs_params_check(const hs_params *p);
  * codes: host, offsets[n_seqs] residue codes; sequence i is
  * codes[offsets[i] .. offsets[i+1]); offsets: host, n_seqs+1 entries,
  * offsets[0] == 0, non-decreasing; empty sequences are allowed.  The
- * library copies both to the device (the caller keeps its buffers), orders
- * the sequences by length on the device for scheduling, and returns a
- * handle in *out.  Errors: HS_EINVAL (bad offsets or codes >= 24),
+ * library copies both to the device (the caller keeps its buffers), keeps
+ * a longest-first scheduling order of the sequences next to them, and
+ * returns a handle in *out.  Errors: HS_EINVAL (bad offsets or codes >= 24),
  * HS_ETOOLONG (a sequence longer than HS_MAX_SEQ_LEN), HS_ENOMEM, HS_ECUDA. */
 int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs,
                void *stream, hs_db **out);
@@ -163,6 +163,21 @@ int hs_get_alignment(hs_db *db, const uint8_t *query, int32_t qlen, const hs_par
                      uint64_t seed, int64_t db_index, void *stream,
                      uint32_t *ops_out, int64_t cap, int32_t *score_out,
                      int64_t *ops_len_out, hs_hit *hit_out);
+
+/* Bytes hs_search moves per call: host->device (the query) and
+ * device->host (hits, status and the ops region), for a query length and k. */
+int hs_search_transfer_bytes(int32_t qlen, int32_t k, int64_t *h2d, int64_t *d2h);
+
+/* Tracing hook (no counterpart in the paper; for profiling).  When set on a
+ * database, every later search on it records scan_start / scan_stop (two
+ * cudaEvent_t created by the caller, or NULL) on its stream around the
+ * database scan, and stores in `launches` the number of kernels the search
+ * launched.  The struct must stay valid while set; NULL clears the hook. */
+typedef struct {
+    void *scan_start, *scan_stop;
+    int32_t launches;
+} hs_trace;
+int hs_db_set_trace(hs_db *db, hs_trace *trace);
 
 /* Static message for a status code. */
 const char *hs_strerror(int status);

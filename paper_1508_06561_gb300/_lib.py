@@ -25,6 +25,10 @@ class hs_params(C.Structure):
                 ("mode", C.c_int32), ("matrix", C.POINTER(C.c_int8))]
 
 
+class hs_trace(C.Structure):
+    _fields_ = [("scan_start", C.c_void_p), ("scan_stop", C.c_void_p), ("launches", C.c_int32)]
+
+
 class HsError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = status
@@ -61,10 +65,13 @@ def lib():
     L.hs_search_device.argtypes = [vp, vp, i32, P(hs_params), i32, u64, vp, vp, sz, vp, vp, i64, vp, vp, vp, vp]
     L.hs_search.argtypes = [vp, vp, i32, P(hs_params), i32, u64, vp, vp, P(i32), vp, i64, P(i64)]
     L.hs_get_alignment.argtypes = [vp, vp, i32, P(hs_params), u64, i64, vp, vp, i64, P(i32), P(i64), vp]
+    L.hs_search_transfer_bytes.argtypes = [i32, i32, P(i64), P(i64)]
+    L.hs_db_set_trace.argtypes = [vp, P(hs_trace)]
     L.hs_strerror.argtypes = [C.c_int]
     L.hs_strerror.restype = C.c_char_p
     for name in ("hs_encode", "hs_builtin_matrix", "hs_params_check", "hs_db_load", "hs_db_info",
-                 "hs_search_workspace_size", "hs_search_device", "hs_search", "hs_get_alignment"):
+                 "hs_search_workspace_size", "hs_search_device", "hs_search", "hs_get_alignment",
+                 "hs_search_transfer_bytes", "hs_db_set_trace"):
         getattr(L, name).restype = C.c_int
     _L = L
     return L

@@ -130,6 +130,7 @@ struct hs_db {
     size_t io_bytes = 0;
     char *h_io = nullptr;                   // pinned mirror of d_io
     size_t h_io_bytes = 0;
+    hs_trace *trace = nullptr;              // optional tracing hook
 };
 
 extern "C" {
@@ -313,10 +314,19 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, cons
     const int64_t split = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= qlen; }) - L.begin();
     const int64_t long_end = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
     DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
-    e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st);
-    if (e == cudaSuccess && nhits > 0) e = launch_topk(ws, db->n, nhits, st);
+    ScanTrace tr{nullptr, nullptr};
+    if (db->trace) {
+        tr.start = static_cast<cudaEvent_t>(db->trace->scan_start);
+        tr.stop = static_cast<cudaEvent_t>(db->trace->scan_stop);
+    }
+    int launches = 0;
+    e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st, db->trace ? &tr : nullptr,
+                    &launches);
+    if (e == cudaSuccess && nhits > 0) e = launch_topk(ws, db->n, nhits, st, &launches);
     if (e == cudaSuccess && nhits > 0)
-        e = launch_replay(v, d_query, kp, ws, nhits, d_hits, d_ops, ops_cap, d_ops_used, d_status, st);
+        e = launch_replay(v, d_query, kp, ws, nhits, d_hits, d_ops, ops_cap, d_ops_used, d_status, st,
+                          &launches);
+    if (db->trace) db->trace->launches = launches;
     return from_cuda(e);
 }
 
@@ -362,6 +372,22 @@ static int ensure_host_state(hs_db *db, size_t ws_need, size_t io_need)
         if (e != cudaSuccess) return from_cuda(e);
         db->h_io_bytes = io_need;
     }
+    return HS_OK;
+}
+
+int hs_search_transfer_bytes(int32_t qlen, int32_t k, int64_t *h2d, int64_t *d2h)
+{
+    if (qlen < 1 || k < 0 || !h2d || !d2h) return HS_EINVAL;
+    const IoLayout l = io_layout(qlen, k);
+    *h2d = qlen;
+    *d2h = (int64_t)(l.total - l.hits);
+    return HS_OK;
+}
+
+int hs_db_set_trace(hs_db *db, hs_trace *trace)
+{
+    if (!db) return HS_EINVAL;
+    db->trace = trace;
     return HS_OK;
 }
 

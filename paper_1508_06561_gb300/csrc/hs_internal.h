@@ -69,14 +69,20 @@ int64_t slot_stride_for(int32_t qlen);
 // Role split: targets at sorted positions [0, split) are at least as long
 // as the query (the query is the small sequence); [split, n) are shorter.
 // long_end: sorted positions [0, long_end) hold targets of >= kLongLen letters.
+// trace (optional): events recorded around the scan launch(es).
+// launches (optional): incremented by the number of kernels launched.
+struct ScanTrace {
+    cudaEvent_t start, stop;
+};
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
-                        cudaStream_t st);
+                        cudaStream_t st, const ScanTrace *trace, int *launches);
 size_t scan_smem_bytes(int32_t qlen);
-cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st);
+cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches);
 cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParams &kp,
                           const Workspace &ws, int32_t nhits, hs_hit *d_hits, uint32_t *d_ops,
-                          int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st);
+                          int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st,
+                          int *launches);
 cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KParams &kp,
                               const Workspace &ws, int64_t db_index, uint32_t *d_ops, int64_t cap,
                               hs_hit *d_hit, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st);

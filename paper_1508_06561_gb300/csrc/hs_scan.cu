@@ -39,56 +39,69 @@ struct ScanRange {
     int64_t begin, long_end, end;   // sorted positions [begin, end); [begin, long_end) long
     uint32_t *ctr_long, *ctr_short;
     int qsmall;                     // role shared by every pair of the range
+    int prof_off;                   // word offset of this role's profile in shared memory
+};
+
+// Up to two ranges (the two roles).  With both profiles resident, one launch
+// drains the long-target range first and then the short one, so the whole
+// database is a single longest-first queue.
+struct ScanPlan {
+    ScanRange rg[2];
+    int nranges;
+    int64_t smem_words;             // profile words to copy from prof_g
 };
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
-scan_kernel(DbView db, ScanRange rg, const uint32_t *__restrict__ prof_g, KParams kp,
+scan_kernel(DbView db, ScanPlan plan, const uint32_t *__restrict__ prof_g, KParams kp,
             int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
     extern __shared__ uint4 smem_raw[];
     uint32_t *prof = reinterpret_cast<uint32_t *>(smem_raw);
     const int S = profile_stride(kp.qlen);
     {
-        const int64_t n16 = profile_words(kp.qlen) / 4;   // words is a multiple of 4
+        const int64_t n16 = plan.smem_words / 4;   // profile words are a multiple of 4
         const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
         for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
     }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    int long_done = rg.long_end <= rg.begin;
-    for (;;) {
-        int64_t start = 0, cnt = 0;
-        if (lane == 0) {
-            if (!long_done) {
-                const int64_t i = rg.begin + (int64_t)atomicAdd(rg.ctr_long, 1u);
-                if (i < rg.long_end) { start = i; cnt = 1; }
-                else long_done = 1;
-            }
-            if (cnt == 0) {
-                start = max(rg.long_end, rg.begin) + (int64_t)atomicAdd(rg.ctr_short, (uint32_t)kShortChunk);
-                cnt = min((int64_t)kShortChunk, rg.end - start);
-            }
-        }
-        start = __shfl_sync(0xFFFFFFFFu, start, 0);
-        cnt = __shfl_sync(0xFFFFFFFFu, cnt, 0);
-        long_done = __shfl_sync(0xFFFFFFFFu, long_done, 0);
-        if (cnt <= 0) break;
-        for (int64_t pos = start; pos < start + cnt; pos++) {
-            const int64_t d = db.order[pos];
-            const int64_t off = db.offsets[d];
-            PairCtx c;
-            c.prof = prof;
-            c.S = S;
-            c.t = db.codes + off;
-            c.tlen = (int32_t)(db.offsets[d + 1] - off);
-            c.qlen = kp.qlen;
-            c.qsmall = rg.qsmall != 0;
-            int64_t cells = 0;
-            const int32_t s = align_pair(c, kp, (uint64_t)d, lane, cells, nullptr);
+    for (int ri = 0; ri < plan.nranges; ri++) {
+        const ScanRange rg = ri == 0 ? plan.rg[0] : plan.rg[1];   // no dynamic param indexing
+        int long_done = rg.long_end <= rg.begin;
+        for (;;) {
+            int64_t start = 0, cnt = 0;
             if (lane == 0) {
-                scores[d] = s;
-                if (cells_out) cells_out[d] = cells;
+                if (!long_done) {
+                    const int64_t i = rg.begin + (int64_t)atomicAdd(rg.ctr_long, 1u);
+                    if (i < rg.long_end) { start = i; cnt = 1; }
+                    else long_done = 1;
+                }
+                if (cnt == 0) {
+                    start = max(rg.long_end, rg.begin) + (int64_t)atomicAdd(rg.ctr_short, (uint32_t)kShortChunk);
+                    cnt = min((int64_t)kShortChunk, rg.end - start);
+                }
+            }
+            start = __shfl_sync(0xFFFFFFFFu, start, 0);
+            cnt = __shfl_sync(0xFFFFFFFFu, cnt, 0);
+            long_done = __shfl_sync(0xFFFFFFFFu, long_done, 0);
+            if (cnt <= 0) break;
+            for (int64_t pos = start; pos < start + cnt; pos++) {
+                const int64_t d = db.order[pos];
+                const int64_t off = db.offsets[d];
+                PairCtx c;
+                c.prof = prof + rg.prof_off;
+                c.S = S;
+                c.t = db.codes + off;
+                c.tlen = (int32_t)(db.offsets[d + 1] - off);
+                c.qlen = kp.qlen;
+                c.qsmall = rg.qsmall != 0;
+                int64_t cells = 0;
+                const int32_t s = align_pair(c, kp, (uint64_t)d, lane, cells, nullptr);
+                if (lane == 0) {
+                    scores[d] = s;
+                    if (cells_out) cells_out[d] = cells;
+                }
             }
         }
     }
@@ -96,38 +109,79 @@ scan_kernel(DbView db, ScanRange rg, const uint32_t *__restrict__ prof_g, KParam
 
 size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
 
+// Both profiles share one launch when they fit twice per SM with room to spare.
+static bool fuse_roles(int32_t qlen) { return 2 * scan_smem_bytes(qlen) <= 100 * 1024; }
+
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
-                        cudaStream_t st)
+                        cudaStream_t st, const ScanTrace *trace, int *launches)
 {
     const int64_t words = profile_words(kp.qlen);
     profile_kernel<<<64, 256, 0, st>>>(d_query, kp, ws.prof);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    int nl = 1;
 
-    const size_t smem = scan_smem_bytes(kp.qlen);
-    e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kWarpsPerCta * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = per_sm * num_sms;
-
+    ScanRange r[2];
     for (int role = 0; role < 2; role++) {
-        ScanRange rg;
+        ScanRange &rg = r[role];
         rg.qsmall = role == 0;
         rg.begin = role == 0 ? 0 : split;
         rg.end = role == 0 ? split : db.n;
         rg.long_end = role == 0 ? min(long_end, split) : rg.begin;
         rg.ctr_long = ws.counters + (role == 0 ? kQsLong : kQlLong);
         rg.ctr_short = ws.counters + (role == 0 ? kQsShort : kQlShort);
-        if (rg.end <= rg.begin) continue;
-        const uint32_t *pg = ws.prof + (role == 0 ? 0 : words);
-        scan_kernel<<<grid, kWarpsPerCta * 32, smem, st>>>(db, rg, pg, kp, ws.scores, d_cells);
-        e = cudaGetLastError();
+        rg.prof_off = 0;
+    }
+    const bool fused = fuse_roles(kp.qlen);
+    ScanPlan plans[2];
+    const uint32_t *srcs[2];
+    int nplans = 0;
+    if (fused) {
+        ScanPlan &pl = plans[nplans];
+        pl.nranges = 0;
+        for (int role = 0; role < 2; role++) {
+            if (r[role].end <= r[role].begin) continue;
+            r[role].prof_off = role == 0 ? 0 : (int)words;
+            pl.rg[pl.nranges++] = r[role];
+        }
+        pl.smem_words = 2 * words;
+        srcs[nplans] = ws.prof;
+        if (pl.nranges) nplans++;
+    } else {
+        for (int role = 0; role < 2; role++) {
+            if (r[role].end <= r[role].begin) continue;
+            ScanPlan &pl = plans[nplans];
+            pl.rg[0] = r[role];
+            pl.nranges = 1;
+            pl.smem_words = words;
+            srcs[nplans] = ws.prof + (role == 0 ? 0 : words);
+            nplans++;
+        }
+    }
+    if (trace && trace->start) {
+        e = cudaEventRecord(trace->start, st);
         if (e != cudaSuccess) return e;
     }
+    for (int i = 0; i < nplans; i++) {
+        const size_t smem = (size_t)plans[i].smem_words * 4;
+        e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kWarpsPerCta * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, plans[i], srcs[i], kp, ws.scores,
+                                                                        d_cells);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        nl++;
+    }
+    if (trace && trace->stop) {
+        e = cudaEventRecord(trace->stop, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (launches) *launches += nl;
     return cudaSuccess;
 }
 
@@ -243,7 +297,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, KP
 
 cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParams &kp,
                           const Workspace &ws, int32_t nhits, hs_hit *d_hits, uint32_t *d_ops,
-                          int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st)
+                          int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st,
+                          int *launches)
 {
     (void)d_query;
     if (nhits <= 0) return cudaSuccess;
@@ -265,6 +320,7 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
     ra.status = d_status;
     const int grid = (nhits + kWarpsPerCta - 1) / kWarpsPerCta;
     replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp, ra);
+    if (launches) *launches += 1;
     return cudaGetLastError();
 }
 

@@ -170,11 +170,12 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
 
 }  // namespace
 
-cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st)
+cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches)
 {
     if (n <= 0 || k <= 0) return cudaSuccess;
     topk_kernel<<<ws.topk_ctas, kTopkThreads, 0, st>>>(ws.scores, n, k, ws.cand, ws.hit_idx, ws.hit_score,
                                                        ws.counters + kTopkTicket);
+    if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
