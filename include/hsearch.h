@@ -144,6 +144,32 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen,
                      hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
                      int32_t *d_scores, int64_t *d_cells, int32_t *d_status);
 
+/* hs_search_device without allocation (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory at search time, such as
+ * a process whose memory manager reserved all device memory up front, a
+ * serving loop that cannot afford cudaMalloc's implicit synchronisation, or a
+ * host that forbids allocation after start-up).  Same arguments and results
+ * as hs_search_device, minus the workspace: the scratch is a fixed array of
+ * HS_NOALLOC_SCRATCH_BYTES inside the library's device image, which every
+ * GPU that loads the library holds until the process exits.  The call makes
+ * no cudaMalloc/cudaFree and no allocating library call; the database (from
+ * hs_db_load) and every output buffer come from the caller.
+ *   - Sizes: HS_ETRUNC if hs_search_workspace_size(db, qlen, k) exceeds
+ *     HS_NOALLOC_SCRATCH_BYTES (8 MiB: e.g. ~1.5M targets for a 256-residue
+ *     query and k = 100).
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   - Sharing: all calls on a device use the same array, which keeps the last
+ *     call's contents; each call clears what must start at zero.  Calls
+ *     whose work overlaps on the GPU (other streams, other threads) race on
+ *     it: serialise them. */
+#define HS_NOALLOC_SCRATCH_BYTES (8 << 20)
+int hs_search_device_noalloc(const hs_db *db, const uint8_t *d_query, int32_t qlen,
+                             const hs_params *p, int32_t k, uint64_t seed, void *stream,
+                             hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
+                             int32_t *d_scores, int64_t *d_cells, int32_t *d_status);
+
 /* The same search from host buffers: copies the query (host, qlen codes) in,
  * runs on `stream`, copies the hits and ops back and synchronises.
  *   hits_out : host, room for min(k, n_seqs) records; *n_hits_out receives

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import HIT_DTYPE, HS_OP_D, HS_OP_I, HS_OP_M, HsError, check, lib
 
-__all__ = ["Params", "Database", "search", "search_device", "get_alignment", "encode",
+__all__ = ["Params", "Database", "search", "search_device", "search_device_noalloc", "get_alignment", "encode",
            "builtin_matrix", "ops_to_rows", "HIT_DTYPE", "HsError", "workspace_size"]
 
 GAP = 0xFF
@@ -166,6 +166,27 @@ def search_device(db: Database, query, k: int, params: Params | None = None, see
         out["cells"].data_ptr() if "cells" in out else None,
         out["status"].data_ptr()), "hs_search_device")
     out["n_hits"] = nh
+    return out
+
+
+def search_device_noalloc(db: Database, query, k: int, out, params: Params | None = None, seed: int = 0,
+                          stream=None):
+    """hs_search_device_noalloc: the device search for callers that cannot
+    allocate device memory while searching.  `out` must hold preallocated
+    CUDA tensors "hits", "ops", "ops_used", "status" (and optionally
+    "scores", "cells"), e.g. a previous search_device result; nothing is
+    allocated here.  Scratch is the library's fixed 8 MiB area."""
+    import torch
+    qlen = int(query.numel())
+    p, _keep = (params or Params()).to_c()
+    st = stream if stream is not None else torch.cuda.current_stream(query.device)
+    check(lib().hs_search_device_noalloc(
+        db.handle, query.data_ptr(), qlen, C.byref(p), k, seed & (2**64 - 1), _stream_ptr(st),
+        out["hits"].data_ptr(), out["ops"].data_ptr(), int(out["ops"].numel()), out["ops_used"].data_ptr(),
+        out["scores"].data_ptr() if "scores" in out else None,
+        out["cells"].data_ptr() if "cells" in out else None,
+        out["status"].data_ptr()), "hs_search_device_noalloc")
+    out["n_hits"] = min(k, db.n)
     return out
 
 

@@ -13,6 +13,7 @@ HS_MODE_DB = 0
 HS_OP_M, HS_OP_I, HS_OP_D = 0, 1, 2
 HS_MAX_QUERY_LEN = 2048
 HS_MAX_K = 4096
+HS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 HIT_DTYPE = np.dtype([("db_index", "<i8"), ("score", "<i4"), ("q_begin", "<i4"), ("q_end", "<i4"),
                       ("t_begin", "<i4"), ("t_end", "<i4"), ("ops_len", "<i4"), ("ops_offset", "<i8")])
@@ -65,13 +66,14 @@ def lib():
     L.hs_search_device.argtypes = [vp, vp, i32, P(hs_params), i32, u64, vp, vp, sz, vp, vp, i64, vp, vp, vp, vp]
     L.hs_search.argtypes = [vp, vp, i32, P(hs_params), i32, u64, vp, vp, P(i32), vp, i64, P(i64)]
     L.hs_get_alignment.argtypes = [vp, vp, i32, P(hs_params), u64, i64, vp, vp, i64, P(i32), P(i64), vp]
+    L.hs_search_device_noalloc.argtypes = [vp, vp, i32, P(hs_params), i32, u64, vp, vp, vp, i64, vp, vp, vp, vp]
     L.hs_search_transfer_bytes.argtypes = [i32, i32, P(i64), P(i64)]
     L.hs_db_set_trace.argtypes = [vp, P(hs_trace)]
     L.hs_strerror.argtypes = [C.c_int]
     L.hs_strerror.restype = C.c_char_p
     for name in ("hs_encode", "hs_builtin_matrix", "hs_params_check", "hs_db_load", "hs_db_info",
                  "hs_search_workspace_size", "hs_search_device", "hs_search", "hs_get_alignment",
-                 "hs_search_transfer_bytes", "hs_db_set_trace"):
+                 "hs_search_transfer_bytes", "hs_db_set_trace", "hs_search_device_noalloc"):
         getattr(L, name).restype = C.c_int
     _L = L
     return L

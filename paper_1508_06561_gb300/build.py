@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhsearch.so")
-SOURCES = ["hs_api.cu", "hs_scan.cu", "hs_topk.cu"]
+SOURCES = ["hs_api.cu", "hs_scan.cu", "hs_topk.cu", "hs_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
