@@ -95,14 +95,101 @@ __device__ __forceinline__ uint32_t profile_word_value(const uint8_t *q, int qle
 // One getBestSubsequenceAlignment call in database mode (Sec. III.B.3 b):
 // shifts k = 0 .. ls-ss; V(k) = sum over the ss letters of the small piece of
 // M against the large piece shifted by k (the virtual score, no gaps).
-// Returns, uniform over the warp, the best V and the lowest k attaining it.
+//
+// Work unit: a "chunk" of 4 adjacent shifts k0..k0+3 held in the 4 byte
+// lanes of one register.  A chunk's cells are visited by an iteration index:
+//   query large (fwd): iteration j = small letter; row = target letter
+//     t[Sp+j], stored query column Lp+k0+j+4 (byte w <-> shift k0+w);
+//   query small (rev): iteration p = large position relative to k0; row =
+//     target letter t[Lp+k0+p], stored reversed-query column qlen+3-Sp-p;
+//     byte w holds a real cell only while 0 <= p-w < ss, so iterations
+//     p < 3 and p >= ss are masked (p runs over [0, ss+3)).
+// Byte lanes hold biased cells (M+bias >= 0); they are widened into 32-bit
+// sums every `flush` iterations, before any byte can overflow.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void spread_bytes(uint32_t acc, uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t &a3)
+struct Acc4 {
+    uint32_t a0, a1, a2, a3;
+};
+
+__device__ __forceinline__ void spread(uint32_t x, Acc4 &A)
 {
-    a0 += acc & 0xFFu;
-    a1 += (acc >> 8) & 0xFFu;
-    a2 += (acc >> 16) & 0xFFu;
-    a3 += acc >> 24;
+    A.a0 += x & 0xFFu;
+    A.a1 += (x >> 8) & 0xFFu;
+    A.a2 += (x >> 16) & 0xFFu;
+    A.a3 += x >> 24;
+}
+
+__device__ __forceinline__ uint32_t prof_word(const uint32_t *prof, int S, int a, int s)
+{
+    return prof[((s & 3) * kNSym + a) * S + (s >> 2)];
+}
+
+// bytes w with w <= p and p - w < ss
+__device__ __forceinline__ uint32_t edge_mask(int p, int ss)
+{
+    const uint32_t lo = p >= 3 ? 0xFFFFFFFFu : (0xFFFFFFFFu >> (8 * (3 - p)));
+    const int h = p - ss + 1;
+    const uint32_t hi = h <= 0 ? 0xFFFFFFFFu : (h >= 4 ? 0u : (0xFFFFFFFFu << (8 * h)));
+    return lo & hi;
+}
+
+__device__ __forceinline__ void rev_masked(const uint32_t *prof, int S, const uint8_t *tl, int sbase, int ss,
+                                           int pa, int pb, int flush, Acc4 &A)
+{
+    uint32_t x = 0;
+    int n = 0;
+    for (int p = pa; p < pb; p++) {
+        x += prof_word(prof, S, tl[p], sbase - p) & edge_mask(p, ss);
+        if (++n == flush) { spread(x, A); x = 0; n = 0; }
+    }
+    spread(x, A);
+}
+
+__device__ __forceinline__ void rev_main(const uint32_t *prof, int S, const uint8_t *tl, int sbase, int pa,
+                                         int pb, int flush, Acc4 &A)
+{
+    for (int c = pa; c < pb; c += 2 * flush) {      // x and y each take <= flush cells
+        const int ce = min(pb, c + 2 * flush);
+        uint32_t x = 0, y = 0;
+        int p = c;
+        for (; p + 1 < ce; p += 2) {
+            x += prof_word(prof, S, tl[p], sbase - p);
+            y += prof_word(prof, S, tl[p + 1], sbase - p - 1);
+        }
+        if (p < ce) x += prof_word(prof, S, tl[p], sbase - p);
+        spread(x, A);
+        spread(y, A);
+    }
+}
+
+// iterations [it0, it1) of a query-small chunk
+__device__ __forceinline__ void rev_chunk(const uint32_t *prof, int S, const uint8_t *tl, int sbase, int ss,
+                                          int it0, int it1, int flush, Acc4 &A)
+{
+    const int e1 = min(it1, 3);
+    if (it0 < e1) rev_masked(prof, S, tl, sbase, ss, it0, e1, flush, A);
+    const int m0 = max(it0, 3), m1 = min(it1, ss);
+    if (m0 < m1) rev_main(prof, S, tl, sbase, m0, m1, flush, A);
+    const int t0 = max(it0, max(3, ss));
+    if (t0 < it1) rev_masked(prof, S, tl, sbase, ss, t0, it1, flush, A);
+}
+
+// iterations [it0, it1) of a query-large chunk (no edges)
+__device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int S, const uint8_t *ts, int s0, int it0, int it1,
+                                          int flush, Acc4 &A)
+{
+    for (int c = it0; c < it1; c += 2 * flush) {    // x and y each take <= flush cells
+        const int ce = min(it1, c + 2 * flush);
+        uint32_t x = 0, y = 0;
+        int j = c;
+        for (; j + 1 < ce; j += 2) {
+            x += prof_word(prof, S, ts[j], s0 + j);
+            y += prof_word(prof, S, ts[j + 1], s0 + j + 1);
+        }
+        if (j < ce) x += prof_word(prof, S, ts[j], s0 + j);
+        spread(x, A);
+        spread(y, A);
+    }
 }
 
 __device__ __forceinline__ void lane_best1(uint32_t acc, int k, int nshift, int32_t off, int32_t &bv, int32_t &bk)
@@ -111,14 +198,13 @@ __device__ __forceinline__ void lane_best1(uint32_t acc, int k, int nshift, int3
     if (k < nshift && v > bv) { bv = v; bk = k; }
 }
 
-// shifts ascend within a lane, so a strict '>' keeps the lowest k
-__device__ __forceinline__ void lane_best(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, int k0,
-                                          int nshift, int32_t off, int32_t &bv, int32_t &bk)
+// shifts ascend within a chunk, so a strict '>' keeps the lowest k
+__device__ __forceinline__ void lane_best(const Acc4 &A, int k0, int nshift, int32_t off, int32_t &bv, int32_t &bk)
 {
-    lane_best1(a0, k0, nshift, off, bv, bk);
-    lane_best1(a1, k0 + 1, nshift, off, bv, bk);
-    lane_best1(a2, k0 + 2, nshift, off, bv, bk);
-    lane_best1(a3, k0 + 3, nshift, off, bv, bk);
+    lane_best1(A.a0, k0, nshift, off, bv, bk);
+    lane_best1(A.a1, k0 + 1, nshift, off, bv, bk);
+    lane_best1(A.a2, k0 + 2, nshift, off, bv, bk);
+    lane_best1(A.a3, k0 + 3, nshift, off, bv, bk);
 }
 
 __device__ __forceinline__ void warp_argmax(int32_t bv, int32_t bk, int32_t &vmax, int32_t &kstar)
@@ -127,76 +213,65 @@ __device__ __forceinline__ void warp_argmax(int32_t bv, int32_t bk, int32_t &vma
     kstar = __reduce_min_sync(0xFFFFFFFFu, bv == vmax ? bk : INT_MAX);
 }
 
-// Query is the large sequence: large piece = Q[Lp, Lp+ls), small piece =
-// tsmall[0, ss) (target letters).  Cells are grouped by small letter j: the
-// row is the target letter tsmall[j], shared by all lanes, and lane's 4
-// shifts read 4 consecutive query columns Lp+k0+j .. +3.
-__device__ __forceinline__ void scan_fwd(const uint32_t *prof, int S, const uint8_t *tsmall, int Lp,
-                                         int ls, int ss, int bias, int flush, int lane,
-                                         int32_t &vmax, int32_t &kstar)
+// One step's window, as seen by whoever scans it.
+struct StepGeo {
+    const uint8_t *t;     // target letters
+    int qsmall;           // the query is the small sequence
+    int Lp, Sp, ls, ss;
+};
+
+// The whole warp scans one step.  Lanes form a Gk x Gj grid: Gk chunks of 4
+// shifts side by side, each chunk's iterations split into Gj contiguous
+// segments whose byte sums are added across the Gj lanes by shuffles.  Gk is
+// the smallest power of two covering the shifts (at most 32, then several
+// passes); Gj takes the remaining lanes while each keeps >= 8 iterations.
+__device__ __forceinline__ void coop_scan(const uint32_t *prof, int S, int qlen, const StepGeo &g, int bias,
+                                          int flush, int lane, int32_t &vmax, int32_t &kstar)
 {
-    const int nshift = ls - ss + 1;
+    const int nshift = g.ls - g.ss + 1;
+    const int nchunk = (nshift + 3) >> 2;
+    const int niter = g.qsmall ? g.ss + 3 : g.ss;
+    const int lgk = nchunk >= 32 ? 5 : 32 - __clz(nchunk - 1);
+    int lgj = 5 - lgk;
+    while (lgj > 0 && niter < (8 << lgj)) lgj--;
+    const int Gk = 1 << lgk, Gj = 1 << lgj;
+    const int gk = lane >> lgj, gj = lane & (Gj - 1);
+    const bool in_grid = lane < (Gk << lgj);
+    const int it0 = (gj * niter) >> lgj, it1 = ((gj + 1) * niter) >> lgj;
+    const int32_t off = bias * g.ss;
+    const int sbase = qlen + 3 - g.Sp;
     int32_t bv = INT_MIN, bk = INT_MAX;
-    for (int base = 0; base < nshift; base += 128) {
-        const int k0 = base + 4 * lane;
-        const bool active = k0 < nshift;
-        const int s0 = active ? Lp + k0 + 4 : 4;
-        uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int j0 = 0; j0 < ss; j0 += flush) {
-            const int jend = min(ss, j0 + flush);
-            uint32_t acc = 0;
-            for (int j = j0; j < jend; j++) {
-                const int a = tsmall[j];
-                const int s = s0 + j;
-                acc += prof[((s & 3) * kNSym + a) * S + (s >> 2)];
-            }
-            spread_bytes(acc, a0, a1, a2, a3);
+    for (int base = 0; base < nshift; base += 4 * Gk) {
+        const int k0 = base + 4 * gk;
+        const bool live = in_grid && k0 < nshift;
+        Acc4 A = {0u, 0u, 0u, 0u};
+        if (live) {
+            if (g.qsmall) rev_chunk(prof, S, g.t + g.Lp + k0, sbase, g.ss, it0, it1, flush, A);
+            else fwd_chunk(prof, S, g.t + g.Sp, g.Lp + k0 + 4, it0, it1, flush, A);
         }
-        if (active) lane_best(a0, a1, a2, a3, k0, nshift, bias * ss, bv, bk);
+        for (int o = 1; o < Gj; o <<= 1) {
+            A.a0 += __shfl_xor_sync(0xFFFFFFFFu, A.a0, o);
+            A.a1 += __shfl_xor_sync(0xFFFFFFFFu, A.a1, o);
+            A.a2 += __shfl_xor_sync(0xFFFFFFFFu, A.a2, o);
+            A.a3 += __shfl_xor_sync(0xFFFFFFFFu, A.a3, o);
+        }
+        if (live && gj == 0) lane_best(A, k0, nshift, off, bv, bk);
     }
     warp_argmax(bv, bk, vmax, kstar);
 }
 
-// Query is the small sequence: large piece = tlarge[0, ls) (target letters),
-// small piece = Q[Sp, Sp+ss).  Cells are grouped by large position p relative
-// to the lane's first shift: the row is the target letter tlarge[k0+p] and
-// the 4 shifts k0+w read reversed-query columns qlen-1-(Sp+p-w), i.e. 4
-// consecutive stored columns.  Byte w holds a real cell only while
-// 0 <= p-w < ss, so the first and last 3 positions are masked.
-__device__ __forceinline__ void scan_rev(const uint32_t *prof, int S, const uint8_t *tlarge, int qlen,
-                                         int Sp, int ls, int ss, int bias, int flush, int lane,
-                                         int32_t &vmax, int32_t &kstar)
+// One lane scans a whole step alone (at most 4 shifts: one chunk).
+__device__ __forceinline__ void lane_scan(const uint32_t *prof, int S, int qlen, const StepGeo &g, int bias,
+                                          int flush, int32_t &vmax, int32_t &kstar)
 {
-    const int nshift = ls - ss + 1;
-    const int sbase = qlen + 3 - Sp;        // stored column of (p = 0, w = 0)
+    const int nshift = g.ls - g.ss + 1;
+    Acc4 A = {0u, 0u, 0u, 0u};
+    if (g.qsmall) rev_chunk(prof, S, g.t + g.Lp, qlen + 3 - g.Sp, g.ss, 0, g.ss + 3, flush, A);
+    else fwd_chunk(prof, S, g.t + g.Sp, g.Lp + 4, 0, g.ss, flush, A);
     int32_t bv = INT_MIN, bk = INT_MAX;
-    for (int base = 0; base < nshift; base += 128) {
-        const int k0 = base + 4 * lane;
-        const bool active = k0 < nshift;
-        const uint8_t *tk = tlarge + (active ? k0 : 0);
-        uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, acc = 0;
-        int since = 0;
-        for (int p = 0; p <= ss + 2; p++) {
-            const int a = tk[p];
-            const int s = sbase - p;
-            uint32_t word = prof[((s & 3) * kNSym + a) * S + (s >> 2)];
-            if (p < 3 || p >= ss) {
-                const uint32_t lo = p >= 3 ? 0xFFFFFFFFu : (0xFFFFFFFFu >> (8 * (3 - p)));
-                const int h = p - ss + 1;
-                const uint32_t hi = h <= 0 ? 0xFFFFFFFFu : (h >= 4 ? 0u : (0xFFFFFFFFu << (8 * h)));
-                word &= lo & hi;
-            }
-            acc += word;
-            if (++since == flush) {
-                spread_bytes(acc, a0, a1, a2, a3);
-                acc = 0;
-                since = 0;
-            }
-        }
-        spread_bytes(acc, a0, a1, a2, a3);
-        if (active) lane_best(a0, a1, a2, a3, k0, nshift, bias * ss, bv, bk);
-    }
-    warp_argmax(bv, bk, vmax, kstar);
+    lane_best(A, 0, nshift, bias * g.ss, bv, bk);
+    vmax = bv;
+    kstar = bk;
 }
 
 // ---------------------------------------------------------------------------
@@ -267,10 +342,8 @@ __device__ __forceinline__ int32_t align_round(const PairCtx &c, const KParams &
         int64_t ssw = (int64_t)(((uint64_t)Srem * sf * u) >> 32);
         const int32_t ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
         int32_t vmax, kstar;
-        if (c.qsmall)
-            scan_rev(c.prof, c.S, c.t + Lp, c.qlen, Sp, ls, ss, kp.bias, kp.flush, lane, vmax, kstar);
-        else
-            scan_fwd(c.prof, c.S, c.t + Sp, Lp, ls, ss, kp.bias, kp.flush, lane, vmax, kstar);
+        const StepGeo g = {c.t, c.qsmall ? 1 : 0, Lp, Sp, ls, ss};
+        coop_scan(c.prof, c.S, c.qlen, g, kp.bias, kp.flush, lane, vmax, kstar);
         cells += (int64_t)(ls - ss + 1) * ss;
         int32_t gap = 0;
         if (kstar > 0) gap = (t == 0) ? kp.pgp * kstar : kp.gop + (kstar - 1) * kp.gep;

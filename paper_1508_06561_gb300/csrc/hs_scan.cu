@@ -30,79 +30,179 @@ __global__ void profile_kernel(const uint8_t *__restrict__ q, KParams kp, uint32
 }
 
 // ---------------------------------------------------------------------------
-// The scan.  A persistent grid; each warp repeatedly takes work from a queue
-// over the length-ordered database (longest first): targets of at least
-// kLongLen letters one at a time, the rest kShortChunk at a time.  Every
-// pair writes only its score (and, if asked, its cell count).
+// The scan.  A persistent grid over one queue of length-ordered database
+// positions (longest first).  Every lane of a warp owns one pair: its O(1)
+// state (Sec. III.B.4) -- positions, step, score, best round, size factors,
+// one cached Philox block -- sits in that lane's registers, so the step
+// bookkeeping of 32 pairs runs as one SIMT instruction stream.  Each round of
+// the loop plans one step for every held pair; steps with at most 4 shifts
+// and 16 small letters are scored by their own lane, the others one at a
+// time by the whole warp (coop_scan).  Targets of >= kLongLen letters are
+// taken one per warp (only lane 0 holds a pair) so each gets the warp alone.
 // ---------------------------------------------------------------------------
-struct ScanRange {
+constexpr int kTinySS = 16;
+
+struct ScanQueue {
     int64_t begin, long_end, end;   // sorted positions [begin, end); [begin, long_end) long
-    uint32_t *ctr_long, *ctr_short;
-    int qsmall;                     // role shared by every pair of the range
-    int prof_off;                   // word offset of this role's profile in shared memory
+    uint32_t *ctr;
+    int64_t smem_words;             // profile words staged into shared memory
+    int rev_off, fwd_off;           // word offsets of the two role profiles (-1: absent)
 };
 
-// Up to two ranges (the two roles).  With both profiles resident, one launch
-// drains the long-target range first and then the short one, so the whole
-// database is a single longest-first queue.
-struct ScanPlan {
-    ScanRange rg[2];
-    int nranges;
-    int64_t smem_words;             // profile words to copy from prof_g
+struct Lane {                       // one pair held by one lane
+    int64_t d;                      // database index, -1 = empty
+    const uint8_t *t;
+    int32_t nl, ns, qsmall;
+    int32_t Lp, Sp, step, score, best, round;
+    uint32_t lf, sf;
+    int64_t cells;
+    int64_t blk;                    // Philox block cached in w0..w3
+    uint64_t w0, w1, w2, w3;
 };
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
-scan_kernel(DbView db, ScanPlan plan, const uint32_t *__restrict__ prof_g, KParams kp,
+__device__ __forceinline__ uint32_t lane_draw(Lane &L, const KParams &kp, uint64_t i)
+{
+    const int64_t b = (int64_t)(i >> 4);
+    if (b != L.blk) {
+        uint64_t o[4];
+        philox4x64_10((uint64_t)L.d, (uint64_t)L.round, (uint64_t)b, 0, kp.seed, 0, o);
+        L.w0 = o[0]; L.w1 = o[1]; L.w2 = o[2]; L.w3 = o[3];
+        L.blk = b;
+    }
+    const unsigned wi = (unsigned)(i >> 2) & 3u;
+    const uint64_t w = wi == 0 ? L.w0 : wi == 1 ? L.w1 : wi == 2 ? L.w2 : L.w3;
+    return (uint32_t)(w >> (48 - 16 * (unsigned)(i & 3))) & 0xFFFFu;
+}
+
+// Start round L.round: lf = MAX(minFactor, LFactor*random()), sf likewise.
+__device__ __forceinline__ void lane_start_round(Lane &L, const KParams &kp)
+{
+    L.blk = -1;
+    uint32_t lf = (uint32_t)(((uint64_t)kp.lf_q16 * lane_draw(L, kp, 0)) >> 16);
+    uint32_t sf = (uint32_t)(((uint64_t)kp.sf_q16 * lane_draw(L, kp, 1)) >> 16);
+    L.lf = max(lf, kp.minf_q16);
+    L.sf = max(sf, kp.minf_q16);
+    L.Lp = 0; L.Sp = 0; L.step = 0; L.score = 0;
+}
+
+// Finish every round whose loop has ended (Fig. 1: "append the remaining
+// with dashes"; AlignSequences keeps the first best round), then the pair.
+__device__ __forceinline__ void lane_settle(Lane &L, const KParams &kp, int32_t *scores, int64_t *cells_out)
+{
+    while (L.d >= 0 && !(L.Lp < L.nl && L.Sp < L.ns)) {
+        L.score -= kp.pgp * ((L.nl - L.Lp) + (L.ns - L.Sp));
+        if (L.score > L.best) L.best = L.score;
+        L.round++;
+        if (L.round < kp.rounds) {
+            lane_start_round(L, kp);
+        } else {
+            scores[L.d] = L.best;
+            if (cells_out) cells_out[L.d] = L.cells;
+            L.d = -1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
+scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParams kp,
             int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
     extern __shared__ uint4 smem_raw[];
-    uint32_t *prof = reinterpret_cast<uint32_t *>(smem_raw);
+    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
     const int S = profile_stride(kp.qlen);
     {
-        const int64_t n16 = plan.smem_words / 4;   // profile words are a multiple of 4
+        const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
         const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
         for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
     }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    for (int ri = 0; ri < plan.nranges; ri++) {
-        const ScanRange rg = ri == 0 ? plan.rg[0] : plan.rg[1];   // no dynamic param indexing
-        int long_done = rg.long_end <= rg.begin;
-        for (;;) {
-            int64_t start = 0, cnt = 0;
-            if (lane == 0) {
-                if (!long_done) {
-                    const int64_t i = rg.begin + (int64_t)atomicAdd(rg.ctr_long, 1u);
-                    if (i < rg.long_end) { start = i; cnt = 1; }
-                    else long_done = 1;
-                }
-                if (cnt == 0) {
-                    start = max(rg.long_end, rg.begin) + (int64_t)atomicAdd(rg.ctr_short, (uint32_t)kShortChunk);
-                    cnt = min((int64_t)kShortChunk, rg.end - start);
-                }
-            }
-            start = __shfl_sync(0xFFFFFFFFu, start, 0);
-            cnt = __shfl_sync(0xFFFFFFFFu, cnt, 0);
-            long_done = __shfl_sync(0xFFFFFFFFu, long_done, 0);
-            if (cnt <= 0) break;
-            for (int64_t pos = start; pos < start + cnt; pos++) {
-                const int64_t d = db.order[pos];
-                const int64_t off = db.offsets[d];
-                PairCtx c;
-                c.prof = prof + rg.prof_off;
-                c.S = S;
-                c.t = db.codes + off;
-                c.tlen = (int32_t)(db.offsets[d + 1] - off);
-                c.qlen = kp.qlen;
-                c.qsmall = rg.qsmall != 0;
-                int64_t cells = 0;
-                const int32_t s = align_pair(c, kp, (uint64_t)d, lane, cells, nullptr);
-                if (lane == 0) {
-                    scores[d] = s;
-                    if (cells_out) cells_out[d] = cells;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    Lane L = {};
+    L.d = -1;
+    L.t = db.codes;
+    L.best = INT_MIN;
+    int phase = qu.long_end > qu.begin ? 0 : 1;       // 0: one long target per warp
+    bool open = true;
+    for (;;) {
+        // refill empty lanes from the queue
+        if (open) {
+            unsigned need = __ballot_sync(0xFFFFFFFFu, L.d < 0);
+            if (phase == 0) need &= 1u;
+            if (need) {
+                const int m = __popc(need);
+                long long base = 0;
+                if (lane == 0) base = (long long)qu.begin + (long long)atomicAdd(qu.ctr, (uint32_t)m);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base + m >= qu.end) open = false;
+                if (phase == 0 && base >= qu.long_end) phase = 1;
+                const long long pos = base + __popc(need & lt_mask);
+                if (((need >> lane) & 1u) && pos < qu.end) {
+                    L.d = db.order[pos];
+                    const int64_t off = db.offsets[L.d];
+                    const int32_t tlen = (int32_t)(db.offsets[L.d + 1] - off);
+                    L.t = db.codes + off;
+                    L.qsmall = tlen >= kp.qlen;            // the target is large on ties
+                    L.nl = L.qsmall ? tlen : kp.qlen;
+                    L.ns = L.qsmall ? kp.qlen : tlen;
+                    L.round = 0;
+                    L.best = INT_MIN;
+                    L.cells = 0;
+                    lane_start_round(L, kp);
+                    lane_settle(L, kp, scores, cells_out);   // empty small sequence
                 }
             }
+        }
+        __syncwarp();
+        const bool busy = L.d >= 0;
+        if (!open && __ballot_sync(0xFFFFFFFFu, busy) == 0) break;
+
+        // plan one step per held pair (Fig. 1's Align: ls and ss, A6)
+        StepGeo g = {L.t, L.qsmall, L.Lp, L.Sp, 1, 1};
+        int32_t vmax = 0, kstar = 0;
+        bool tiny = false;
+        if (busy) {
+            const int32_t Lrem = L.nl - L.Lp, Srem = L.ns - L.Sp;
+            const int32_t ls = max((int32_t)(((uint64_t)Lrem * L.lf) >> 16), 1);
+            const uint64_t u = lane_draw(L, kp, 2 + (uint64_t)L.step);
+            const int64_t ssw = (int64_t)(((uint64_t)Srem * L.sf * u) >> 32);
+            g.ls = ls;
+            g.ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
+            tiny = (ls - g.ss) < 4 && g.ss <= kTinySS;
+            if (tiny) {
+                lane_scan(prof + (L.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, g, kp.bias, kp.flush,
+                          vmax, kstar);
+            }
+        }
+        __syncwarp();
+        // the other steps, one pair at a time, by the whole warp
+        unsigned coop = __ballot_sync(0xFFFFFFFFu, busy && !tiny);
+        while (coop) {
+            const int i = __ffs(coop) - 1;
+            coop &= coop - 1;
+            StepGeo h;
+            h.t = reinterpret_cast<const uint8_t *>(
+                __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(g.t), i));
+            h.qsmall = __shfl_sync(0xFFFFFFFFu, g.qsmall, i);
+            h.Lp = __shfl_sync(0xFFFFFFFFu, g.Lp, i);
+            h.Sp = __shfl_sync(0xFFFFFFFFu, g.Sp, i);
+            h.ls = __shfl_sync(0xFFFFFFFFu, g.ls, i);
+            h.ss = __shfl_sync(0xFFFFFFFFu, g.ss, i);
+            int32_t v, k;
+            coop_scan(prof + (h.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, h, kp.bias, kp.flush, lane, v, k);
+            if (lane == i) { vmax = v; kstar = k; }
+        }
+        // consume (Fig. 1: delete the used-up parts) and score incrementally (A17)
+        if (busy) {
+            L.cells += (int64_t)(g.ls - g.ss + 1) * g.ss;
+            int32_t gap = 0;
+            if (kstar > 0) gap = (L.step == 0) ? kp.pgp * kstar : kp.gop + (kstar - 1) * kp.gep;
+            L.score += vmax - gap;
+            L.Lp += kstar + g.ss;
+            L.Sp += g.ss;
+            L.step++;
+            lane_settle(L, kp, scores, cells_out);
         }
     }
 }
@@ -122,57 +222,44 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
     if (e != cudaSuccess) return e;
     int nl = 1;
 
-    ScanRange r[2];
-    for (int role = 0; role < 2; role++) {
-        ScanRange &rg = r[role];
-        rg.qsmall = role == 0;
-        rg.begin = role == 0 ? 0 : split;
-        rg.end = role == 0 ? split : db.n;
-        rg.long_end = role == 0 ? min(long_end, split) : rg.begin;
-        rg.ctr_long = ws.counters + (role == 0 ? kQsLong : kQlLong);
-        rg.ctr_short = ws.counters + (role == 0 ? kQsShort : kQlShort);
-        rg.prof_off = 0;
-    }
-    const bool fused = fuse_roles(kp.qlen);
-    ScanPlan plans[2];
+    ScanQueue qs[2];
     const uint32_t *srcs[2];
-    int nplans = 0;
-    if (fused) {
-        ScanPlan &pl = plans[nplans];
-        pl.nranges = 0;
-        for (int role = 0; role < 2; role++) {
-            if (r[role].end <= r[role].begin) continue;
-            r[role].prof_off = role == 0 ? 0 : (int)words;
-            pl.rg[pl.nranges++] = r[role];
-        }
-        pl.smem_words = 2 * words;
-        srcs[nplans] = ws.prof;
-        if (pl.nranges) nplans++;
+    int nq = 0;
+    if (fuse_roles(kp.qlen)) {
+        ScanQueue &q = qs[nq];
+        q.begin = 0; q.end = db.n; q.long_end = min(long_end, split);
+        q.ctr = ws.counters + kQsLong;
+        q.smem_words = 2 * words; q.rev_off = 0; q.fwd_off = (int)words;
+        srcs[nq++] = ws.prof;
     } else {
-        for (int role = 0; role < 2; role++) {
-            if (r[role].end <= r[role].begin) continue;
-            ScanPlan &pl = plans[nplans];
-            pl.rg[0] = r[role];
-            pl.nranges = 1;
-            pl.smem_words = words;
-            srcs[nplans] = ws.prof + (role == 0 ? 0 : words);
-            nplans++;
+        if (split > 0) {
+            ScanQueue &q = qs[nq];
+            q.begin = 0; q.end = split; q.long_end = min(long_end, split);
+            q.ctr = ws.counters + kQsLong;
+            q.smem_words = words; q.rev_off = 0; q.fwd_off = -1;
+            srcs[nq++] = ws.prof;
+        }
+        if (split < db.n) {
+            ScanQueue &q = qs[nq];
+            q.begin = split; q.end = db.n; q.long_end = split;   // every target is shorter than the query
+            q.ctr = ws.counters + kQlLong;
+            q.smem_words = words; q.rev_off = -1; q.fwd_off = 0;
+            srcs[nq++] = ws.prof + words;
         }
     }
     if (trace && trace->start) {
         e = cudaEventRecord(trace->start, st);
         if (e != cudaSuccess) return e;
     }
-    for (int i = 0; i < nplans; i++) {
-        const size_t smem = (size_t)plans[i].smem_words * 4;
+    for (int i = 0; i < nq; i++) {
+        const size_t smem = (size_t)qs[i].smem_words * 4;
         e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kWarpsPerCta * 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, plans[i], srcs[i], kp, ws.scores,
-                                                                        d_cells);
+        scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp, ws.scores, d_cells);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         nl++;
