@@ -64,23 +64,19 @@ struct DrawStream {
 
 // ---------------------------------------------------------------------------
 // Query profile.  For role `rev` (the query is the small sequence) the
-// profile holds, for every target letter a, the biased scores M[Q[.]][a] with
-// the query reversed; for role `fwd` (the query is the large sequence) in
-// query order.  Stored column s = c + 4 (4 zero columns of padding in front).
-// Four copies r = 0..3, copy r shifted by r bytes, so any 4 consecutive
-// columns are one aligned 32-bit word: columns [s, s+4) of letter a are word
-//   prof[((s & 3) * 24 + a) * S + (s >> 2)].
-// S (words per row) is odd, so the 24 rows of one column fall in 24 distinct
-// shared-memory banks: lanes reading different letters never conflict.
+// profile holds, for every target letter a, the biased scores M[Q[.]][a] + bias
+// along the reversed query; for role `fwd` (the query is the large sequence)
+// along the query.  Stored column s = c + 4 (4 zero columns in front).  Word
+// s of row a packs stored columns s, s+1, s+2, s+3 in its bytes 0..3, so any
+// 4 consecutive columns are one aligned 32-bit load:  prof[a * R + s].
 // ---------------------------------------------------------------------------
-
 __device__ __forceinline__ uint32_t profile_word_value(const uint8_t *q, int qlen, bool rev,
-                                                       const int8_t *m, int bias, int r, int a, int w)
+                                                       const int8_t *m, int bias, int a, int s)
 {
     uint32_t word = 0;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
-        const int c = 4 * w + r + b - 4;
+        const int c = s + b - 4;
         uint32_t v = 0;
         if (c >= 0 && c < qlen) {
             const int qc = q[rev ? qlen - 1 - c : c];
@@ -119,11 +115,6 @@ __device__ __forceinline__ void spread(uint32_t x, Acc4 &A)
     A.a3 += x >> 24;
 }
 
-__device__ __forceinline__ uint32_t prof_word(const uint32_t *prof, int S, int a, int s)
-{
-    return prof[((s & 3) * kNSym + a) * S + (s >> 2)];
-}
-
 // bytes w with w <= p and p - w < ss
 __device__ __forceinline__ uint32_t edge_mask(int p, int ss)
 {
@@ -133,60 +124,87 @@ __device__ __forceinline__ uint32_t edge_mask(int p, int ss)
     return lo & hi;
 }
 
-__device__ __forceinline__ void rev_masked(const uint32_t *prof, int S, const uint8_t *tl, int sbase, int ss,
+// Query-small iterations p in [pa, pb) of a chunk: letter tl[p], stored
+// column sbase - p.  pw = prof + sbase - pa, so iteration p reads
+// pw[tl[p] * R - (p - pa)].
+__device__ __forceinline__ void rev_masked(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
                                            int pa, int pb, int flush, Acc4 &A)
 {
     uint32_t x = 0;
     int n = 0;
     for (int p = pa; p < pb; p++) {
-        x += prof_word(prof, S, tl[p], sbase - p) & edge_mask(p, ss);
+        x += prof[tl[p] * R + sbase - p] & edge_mask(p, ss);
         if (++n == flush) { spread(x, A); x = 0; n = 0; }
     }
     spread(x, A);
 }
 
-__device__ __forceinline__ void rev_main(const uint32_t *prof, int S, const uint8_t *tl, int sbase, int pa,
+__device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int pa,
                                          int pb, int flush, Acc4 &A)
 {
-    for (int c = pa; c < pb; c += 2 * flush) {      // x and y each take <= flush cells
-        const int ce = min(pb, c + 2 * flush);
+    const uint32_t *pw = prof + (sbase - pa);
+    const uint8_t *tp = tl + pa;
+    const int n = pb - pa;
+    for (int c = 0; c < n; c += 2 * flush) {        // x and y each take <= flush cells
+        const int ce = min(n, c + 2 * flush);
         uint32_t x = 0, y = 0;
-        int p = c;
-        for (; p + 1 < ce; p += 2) {
-            x += prof_word(prof, S, tl[p], sbase - p);
-            y += prof_word(prof, S, tl[p + 1], sbase - p - 1);
+        int i = c;
+        for (; i + 1 < ce; i += 2) {
+            x += pw[tp[i] * R - i];
+            y += pw[tp[i + 1] * R - (i + 1)];
         }
-        if (p < ce) x += prof_word(prof, S, tl[p], sbase - p);
+        if (i < ce) x += pw[tp[i] * R - i];
         spread(x, A);
         spread(y, A);
     }
 }
 
-// iterations [it0, it1) of a query-small chunk
-__device__ __forceinline__ void rev_chunk(const uint32_t *prof, int S, const uint8_t *tl, int sbase, int ss,
+// iterations [it0, it1) of a query-small chunk; the 3 first and 3 last
+// iterations of the whole range [0, ss+3) carry partial byte masks
+__device__ __forceinline__ void rev_chunk(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
                                           int it0, int it1, int flush, Acc4 &A)
 {
-    const int e1 = min(it1, 3);
-    if (it0 < e1) rev_masked(prof, S, tl, sbase, ss, it0, e1, flush, A);
-    const int m0 = max(it0, 3), m1 = min(it1, ss);
-    if (m0 < m1) rev_main(prof, S, tl, sbase, m0, m1, flush, A);
-    const int t0 = max(it0, max(3, ss));
-    if (t0 < it1) rev_masked(prof, S, tl, sbase, ss, t0, it1, flush, A);
+    if (ss < 3) {                                   // edges overlap: mask every iteration
+        rev_masked(prof, R, tl, sbase, ss, it0, it1, flush, A);
+        return;
+    }
+    int a = it0, b = it1;
+    if (a == 0) {                                   // p = 0, 1, 2: bytes w <= p
+        const uint32_t w0 = prof[tl[0] * R + sbase] & 0x000000FFu;
+        const uint32_t w1 = prof[tl[1] * R + sbase - 1] & 0x0000FFFFu;
+        const uint32_t w2 = prof[tl[2] * R + sbase - 2] & 0x00FFFFFFu;
+        if (flush >= 3) spread(w0 + w1 + w2, A);
+        else { spread(w0, A); spread(w1, A); spread(w2, A); }
+        a = 3;
+    }
+    if (b == ss + 3) {                              // p = ss, ss+1, ss+2: bytes w > p - ss
+        const uint32_t w0 = prof[tl[ss] * R + sbase - ss] & 0xFFFFFF00u;
+        const uint32_t w1 = prof[tl[ss + 1] * R + sbase - ss - 1] & 0xFFFF0000u;
+        const uint32_t w2 = prof[tl[ss + 2] * R + sbase - ss - 2] & 0xFF000000u;
+        if (flush >= 3) spread(w0 + w1 + w2, A);
+        else { spread(w0, A); spread(w1, A); spread(w2, A); }
+        b = ss;
+    }
+    if (a < b) rev_main(prof, R, tl, sbase, a, b, flush, A);
 }
 
-// iterations [it0, it1) of a query-large chunk (no edges)
-__device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int S, const uint8_t *ts, int s0, int it0, int it1,
+// iterations [it0, it1) of a query-large chunk: letter ts[j], stored column
+// s0 + j (no edges)
+__device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uint8_t *ts, int s0, int it0, int it1,
                                           int flush, Acc4 &A)
 {
-    for (int c = it0; c < it1; c += 2 * flush) {    // x and y each take <= flush cells
-        const int ce = min(it1, c + 2 * flush);
+    const uint32_t *pw = prof + (s0 + it0);
+    const uint8_t *tp = ts + it0;
+    const int n = it1 - it0;
+    for (int c = 0; c < n; c += 2 * flush) {        // x and y each take <= flush cells
+        const int ce = min(n, c + 2 * flush);
         uint32_t x = 0, y = 0;
-        int j = c;
-        for (; j + 1 < ce; j += 2) {
-            x += prof_word(prof, S, ts[j], s0 + j);
-            y += prof_word(prof, S, ts[j + 1], s0 + j + 1);
+        int i = c;
+        for (; i + 1 < ce; i += 2) {
+            x += pw[tp[i] * R + i];
+            y += pw[tp[i + 1] * R + i + 1];
         }
-        if (j < ce) x += prof_word(prof, S, ts[j], s0 + j);
+        if (i < ce) x += pw[tp[i] * R + i];
         spread(x, A);
         spread(y, A);
     }
@@ -224,7 +242,7 @@ struct StepGeo {
 // shifts side by side, each chunk's iterations split into Gj contiguous
 // segments whose byte sums are added across the Gj lanes by shuffles.  Gk is
 // the smallest power of two covering the shifts (at most 32, then several
-// passes); Gj takes the remaining lanes while each keeps >= 8 iterations.
+// passes); Gj takes the remaining lanes while each keeps >= 4 iterations.
 __device__ __forceinline__ void coop_scan(const uint32_t *prof, int S, int qlen, const StepGeo &g, int bias,
                                           int flush, int lane, int32_t &vmax, int32_t &kstar)
 {
@@ -233,7 +251,7 @@ __device__ __forceinline__ void coop_scan(const uint32_t *prof, int S, int qlen,
     const int niter = g.qsmall ? g.ss + 3 : g.ss;
     const int lgk = nchunk >= 32 ? 5 : 32 - __clz(nchunk - 1);
     int lgj = 5 - lgk;
-    while (lgj > 0 && niter < (8 << lgj)) lgj--;
+    while (lgj > 0 && niter < (4 << lgj)) lgj--;   // segments of >= 4 iterations
     const int Gk = 1 << lgk, Gj = 1 << lgj;
     const int gk = lane >> lgj, gj = lane & (Gj - 1);
     const bool in_grid = lane < (Gk << lgj);

@@ -16,11 +16,12 @@ constexpr int kLongLen = 2048;          // targets this long are scheduled one p
 constexpr int kShortChunk = 8;          // shorter targets are taken 8 at a time
 constexpr int kCodesPad = 64;           // readable bytes past the last residue
 
-// Query profile geometry: 4 byte-shifted copies x 24 letters x S words,
-// S odd (so the 24 rows of a column sit in distinct shared-memory banks) and
-// wide enough for 4 zero columns before and 12 after the query.
-__host__ __device__ inline int profile_stride(int qlen) { return ((qlen + 16) >> 2) | 1; }
-__host__ __device__ inline int64_t profile_words(int qlen) { return 4LL * kNSym * profile_stride(qlen); }
+// Query profile geometry: for each of the 24 letters a row of R words,
+// word s packing the biased scores of stored columns s..s+3 (4 zero columns
+// before the query, 12 after).  R is odd, so the 24 rows of one column fall
+// in 24 distinct shared-memory banks.
+__host__ __device__ inline int profile_stride(int qlen) { return (qlen + 16) | 1; }
+__host__ __device__ inline int64_t profile_words(int qlen) { return (int64_t)kNSym * profile_stride(qlen); }
 
 // Everything a kernel needs to score pairs; passed by value as a kernel
 // argument, so launching needs no host->device copy of the parameters.

@@ -16,16 +16,14 @@ __global__ void profile_kernel(const uint8_t *__restrict__ q, KParams kp, uint32
     __shared__ int8_t msm[kNSym * kNSym];
     for (int i = threadIdx.x; i < kNSym * kNSym; i += blockDim.x) msm[i] = kp.m[i];
     __syncthreads();
-    const int S = profile_stride(kp.qlen);
+    const int R = profile_stride(kp.qlen);
     const int64_t words = profile_words(kp.qlen);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * words;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const bool rev = idx < words;
         const int64_t i = rev ? idx : idx - words;
-        const int r = (int)(i / (kNSym * S));
-        const int rem = (int)(i - (int64_t)r * kNSym * S);
-        const int a = rem / S, w = rem - a * S;
-        prof[idx] = profile_word_value(q, kp.qlen, rev, msm, kp.bias, r, a, w);
+        const int a = (int)(i / R), s = (int)(i - (int64_t)a * R);
+        prof[idx] = profile_word_value(q, kp.qlen, rev, msm, kp.bias, a, s);
     }
 }
 
