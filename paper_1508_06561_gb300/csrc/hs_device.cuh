@@ -159,33 +159,35 @@ __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint
     }
 }
 
-// iterations [it0, it1) of a query-small chunk; the 3 first and 3 last
-// iterations of the whole range [0, ss+3) carry partial byte masks
-__device__ __forceinline__ void rev_chunk(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
-                                          int it0, int it1, int flush, Acc4 &A)
+// Iterations [it0, it1) of a query-small chunk, it1 - it0 >= 6 when ss >= 3.
+// The segment's first 3 and last 3 iterations run with byte masks: partial
+// ones where the segment holds the range's first (p < 3) or last (p >= ss)
+// iterations, all-ones elsewhere -- the same instructions on every lane.
+__device__ __forceinline__ void rev_segment(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
+                                            int it0, int it1, bool first, bool last, int flush, Acc4 &A)
 {
     if (ss < 3) {                                   // edges overlap: mask every iteration
         rev_masked(prof, R, tl, sbase, ss, it0, it1, flush, A);
         return;
     }
-    int a = it0, b = it1;
-    if (a == 0) {                                   // p = 0, 1, 2: bytes w <= p
-        const uint32_t w0 = prof[tl[0] * R + sbase] & 0x000000FFu;
-        const uint32_t w1 = prof[tl[1] * R + sbase - 1] & 0x0000FFFFu;
-        const uint32_t w2 = prof[tl[2] * R + sbase - 2] & 0x00FFFFFFu;
-        if (flush >= 3) spread(w0 + w1 + w2, A);
-        else { spread(w0, A); spread(w1, A); spread(w2, A); }
-        a = 3;
+    const uint32_t f0 = first ? 0x000000FFu : ~0u, f1 = first ? 0x0000FFFFu : ~0u, f2 = first ? 0x00FFFFFFu : ~0u;
+    const uint32_t l0 = last ? 0xFFFFFF00u : ~0u, l1 = last ? 0xFFFF0000u : ~0u, l2 = last ? 0xFF000000u : ~0u;
+    const uint32_t *pw = prof + sbase;
+    const uint32_t a0 = pw[tl[it0] * R - it0] & f0;
+    const uint32_t a1 = pw[tl[it0 + 1] * R - (it0 + 1)] & f1;
+    const uint32_t a2 = pw[tl[it0 + 2] * R - (it0 + 2)] & f2;
+    const int e = it1 - 3;
+    const uint32_t b0 = pw[tl[e] * R - e] & l0;
+    const uint32_t b1 = pw[tl[e + 1] * R - (e + 1)] & l1;
+    const uint32_t b2 = pw[tl[e + 2] * R - (e + 2)] & l2;
+    if (flush >= 3) {
+        spread(a0 + a1 + a2, A);
+        spread(b0 + b1 + b2, A);
+    } else {
+        spread(a0, A); spread(a1, A); spread(a2, A);
+        spread(b0, A); spread(b1, A); spread(b2, A);
     }
-    if (b == ss + 3) {                              // p = ss, ss+1, ss+2: bytes w > p - ss
-        const uint32_t w0 = prof[tl[ss] * R + sbase - ss] & 0xFFFFFF00u;
-        const uint32_t w1 = prof[tl[ss + 1] * R + sbase - ss - 1] & 0xFFFF0000u;
-        const uint32_t w2 = prof[tl[ss + 2] * R + sbase - ss - 2] & 0xFF000000u;
-        if (flush >= 3) spread(w0 + w1 + w2, A);
-        else { spread(w0, A); spread(w1, A); spread(w2, A); }
-        b = ss;
-    }
-    if (a < b) rev_main(prof, R, tl, sbase, a, b, flush, A);
+    if (it0 + 3 < e) rev_main(prof, R, tl, sbase, it0 + 3, e, flush, A);
 }
 
 // iterations [it0, it1) of a query-large chunk: letter ts[j], stored column
@@ -231,28 +233,43 @@ __device__ __forceinline__ void warp_argmax(int32_t bv, int32_t bk, int32_t &vma
     kstar = __reduce_min_sync(0xFFFFFFFFu, bv == vmax ? bk : INT_MAX);
 }
 
-// One step's window, as seen by whoever scans it.
-struct StepGeo {
+// One step's window and its lane grid, as seen by whoever scans it.
+struct __align__(16) Plan {
     const uint8_t *t;     // target letters
-    int qsmall;           // the query is the small sequence
-    int Lp, Sp, ls, ss;
+    int32_t Lp, Sp, ls, ss;
+    int32_t qsmall;       // the query is the small sequence
+    int32_t lgk, lgj;     // lane grid: 2^lgk chunks x 2^lgj segments
+    int32_t pad;
 };
 
-// The whole warp scans one step.  Lanes form a Gk x Gj grid: Gk chunks of 4
-// shifts side by side, each chunk's iterations split into Gj contiguous
-// segments whose byte sums are added across the Gj lanes by shuffles.  Gk is
-// the smallest power of two covering the shifts (at most 32, then several
-// passes); Gj takes the remaining lanes while each keeps >= 4 iterations.
-__device__ __forceinline__ void coop_scan(const uint32_t *prof, int S, int qlen, const StepGeo &g, int bias,
-                                          int flush, int lane, int32_t &vmax, int32_t &kstar)
+// Lanes form a Gk x Gj grid: Gk chunks of 4 shifts side by side, each chunk's
+// iterations split into Gj contiguous segments (>= 6 iterations each for
+// query-small steps, whose segments carry 3 masked iterations at both ends;
+// >= 4 otherwise).  Gk is the smallest power of two covering the shifts (at
+// most 32, then several passes); Gj takes what the segments allow of the rest.
+__device__ __forceinline__ void plan_grid(Plan &g)
 {
     const int nshift = g.ls - g.ss + 1;
     const int nchunk = (nshift + 3) >> 2;
-    const int niter = g.qsmall ? g.ss + 3 : g.ss;
     const int lgk = nchunk >= 32 ? 5 : 32 - __clz(nchunk - 1);
-    int lgj = 5 - lgk;
-    while (lgj > 0 && niter < (4 << lgj)) lgj--;   // segments of >= 4 iterations
-    const int Gk = 1 << lgk, Gj = 1 << lgj;
+    const int niter = g.qsmall ? g.ss + 3 : g.ss;
+    const int minseg = g.qsmall ? 6 : 4;
+    int lgj = 0;
+    if (niter >= 2 * minseg) lgj = min(5 - lgk, 31 - __clz(niter / minseg));
+    g.lgk = lgk;
+    g.lgj = lgj;
+}
+
+// The whole warp scans one step (lane grid from plan_grid).  Byte sums of a
+// chunk's segments are added across its Gj lanes by shuffles; the best
+// (V, k) pair over all chunks comes from two warp reductions.
+__device__ __forceinline__ void coop_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
+                                          int flush, int lane, int32_t &vmax, int32_t &kstar)
+{
+    const int nshift = g.ls - g.ss + 1;
+    const int niter = g.qsmall ? g.ss + 3 : g.ss;
+    const int lgj = g.lgj;
+    const int Gk = 1 << g.lgk, Gj = 1 << lgj;
     const int gk = lane >> lgj, gj = lane & (Gj - 1);
     const bool in_grid = lane < (Gk << lgj);
     const int it0 = (gj * niter) >> lgj, it1 = ((gj + 1) * niter) >> lgj;
@@ -264,8 +281,10 @@ __device__ __forceinline__ void coop_scan(const uint32_t *prof, int S, int qlen,
         const bool live = in_grid && k0 < nshift;
         Acc4 A = {0u, 0u, 0u, 0u};
         if (live) {
-            if (g.qsmall) rev_chunk(prof, S, g.t + g.Lp + k0, sbase, g.ss, it0, it1, flush, A);
-            else fwd_chunk(prof, S, g.t + g.Sp, g.Lp + k0 + 4, it0, it1, flush, A);
+            if (g.qsmall)
+                rev_segment(prof, R, g.t + g.Lp + k0, sbase, g.ss, it0, it1, gj == 0, gj == Gj - 1, flush, A);
+            else
+                fwd_chunk(prof, R, g.t + g.Sp, g.Lp + k0 + 4, it0, it1, flush, A);
         }
         for (int o = 1; o < Gj; o <<= 1) {
             A.a0 += __shfl_xor_sync(0xFFFFFFFFu, A.a0, o);
@@ -278,16 +297,19 @@ __device__ __forceinline__ void coop_scan(const uint32_t *prof, int S, int qlen,
     warp_argmax(bv, bk, vmax, kstar);
 }
 
-// One lane scans a whole step alone (at most 4 shifts: one chunk).
-__device__ __forceinline__ void lane_scan(const uint32_t *prof, int S, int qlen, const StepGeo &g, int bias,
+// One lane scans a whole step alone, chunk after chunk.
+__device__ __forceinline__ void lane_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
                                           int flush, int32_t &vmax, int32_t &kstar)
 {
     const int nshift = g.ls - g.ss + 1;
-    Acc4 A = {0u, 0u, 0u, 0u};
-    if (g.qsmall) rev_chunk(prof, S, g.t + g.Lp, qlen + 3 - g.Sp, g.ss, 0, g.ss + 3, flush, A);
-    else fwd_chunk(prof, S, g.t + g.Sp, g.Lp + 4, 0, g.ss, flush, A);
+    const int32_t off = bias * g.ss;
     int32_t bv = INT_MIN, bk = INT_MAX;
-    lane_best(A, 0, nshift, bias * g.ss, bv, bk);
+    for (int k0 = 0; k0 < nshift; k0 += 4) {
+        Acc4 A = {0u, 0u, 0u, 0u};
+        if (g.qsmall) rev_segment(prof, R, g.t + g.Lp + k0, qlen + 3 - g.Sp, g.ss, 0, g.ss + 3, true, true, flush, A);
+        else fwd_chunk(prof, R, g.t + g.Sp, g.Lp + k0 + 4, 0, g.ss, flush, A);
+        lane_best(A, k0, nshift, off, bv, bk);
+    }
     vmax = bv;
     kstar = bk;
 }
@@ -360,7 +382,8 @@ __device__ __forceinline__ int32_t align_round(const PairCtx &c, const KParams &
         int64_t ssw = (int64_t)(((uint64_t)Srem * sf * u) >> 32);
         const int32_t ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
         int32_t vmax, kstar;
-        const StepGeo g = {c.t, c.qsmall ? 1 : 0, Lp, Sp, ls, ss};
+        Plan g = {c.t, Lp, Sp, ls, ss, c.qsmall ? 1 : 0, 0, 0, 0};
+        plan_grid(g);
         coop_scan(c.prof, c.S, c.qlen, g, kp.bias, kp.flush, lane, vmax, kstar);
         cells += (int64_t)(ls - ss + 1) * ss;
         int32_t gap = 0;

@@ -5,7 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/hsearch.h"
+#include "hsearch.h"
 
 namespace hs {
 

@@ -33,12 +33,13 @@ __global__ void profile_kernel(const uint8_t *__restrict__ q, KParams kp, uint32
 // state (Sec. III.B.4) -- positions, step, score, best round, size factors,
 // one cached Philox block -- sits in that lane's registers, so the step
 // bookkeeping of 32 pairs runs as one SIMT instruction stream.  Each round of
-// the loop plans one step for every held pair; steps with at most 4 shifts
-// and 16 small letters are scored by their own lane, the others one at a
-// time by the whole warp (coop_scan).  Targets of >= kLongLen letters are
-// taken one per warp (only lane 0 holds a pair) so each gets the warp alone.
+// the loop plans one step for every held pair.  Small steps (at most
+// kLocalIters chunk iterations) are scored by their own lane; the others one
+// at a time by the whole warp (coop_scan), reading the step's plan from the
+// warp's shared-memory plan slots.  Targets of >= kLongLen letters are taken
+// one per warp (only lane 0 holds a pair) so each gets the warp alone.
 // ---------------------------------------------------------------------------
-constexpr int kTinySS = 16;
+constexpr int kLocalIters = 64;
 
 struct ScanQueue {
     int64_t begin, long_end, end;   // sorted positions [begin, end); [begin, long_end) long
@@ -106,6 +107,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
             int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
     extern __shared__ uint4 smem_raw[];
+    __shared__ Plan plans[kWarpsPerCta][32];
     const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
     const int S = profile_stride(kp.qlen);
     {
@@ -157,9 +159,9 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
         if (!open && __ballot_sync(0xFFFFFFFFu, busy) == 0) break;
 
         // plan one step per held pair (Fig. 1's Align: ls and ss, A6)
-        StepGeo g = {L.t, L.qsmall, L.Lp, L.Sp, 1, 1};
+        Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0};
         int32_t vmax = 0, kstar = 0;
-        bool tiny = false;
+        bool local = false;
         if (busy) {
             const int32_t Lrem = L.nl - L.Lp, Srem = L.ns - L.Sp;
             const int32_t ls = max((int32_t)(((uint64_t)Lrem * L.lf) >> 16), 1);
@@ -167,26 +169,23 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
             const int64_t ssw = (int64_t)(((uint64_t)Srem * L.sf * u) >> 32);
             g.ls = ls;
             g.ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
-            tiny = (ls - g.ss) < 4 && g.ss <= kTinySS;
-            if (tiny) {
+            const int64_t iters = (int64_t)((ls - g.ss + 4) >> 2) * (g.ss + (L.qsmall ? 3 : 0));
+            local = iters <= kLocalIters;
+            if (local) {
                 lane_scan(prof + (L.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, g, kp.bias, kp.flush,
                           vmax, kstar);
+            } else {
+                plan_grid(g);
+                plans[threadIdx.x >> 5][lane] = g;
             }
         }
         __syncwarp();
         // the other steps, one pair at a time, by the whole warp
-        unsigned coop = __ballot_sync(0xFFFFFFFFu, busy && !tiny);
+        unsigned coop = __ballot_sync(0xFFFFFFFFu, busy && !local);
         while (coop) {
             const int i = __ffs(coop) - 1;
             coop &= coop - 1;
-            StepGeo h;
-            h.t = reinterpret_cast<const uint8_t *>(
-                __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(g.t), i));
-            h.qsmall = __shfl_sync(0xFFFFFFFFu, g.qsmall, i);
-            h.Lp = __shfl_sync(0xFFFFFFFFu, g.Lp, i);
-            h.Sp = __shfl_sync(0xFFFFFFFFu, g.Sp, i);
-            h.ls = __shfl_sync(0xFFFFFFFFu, g.ls, i);
-            h.ss = __shfl_sync(0xFFFFFFFFu, g.ss, i);
+            const Plan h = plans[threadIdx.x >> 5][i];
             int32_t v, k;
             coop_scan(prof + (h.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, h, kp.bias, kp.flush, lane, v, k);
             if (lane == i) { vmax = v; kstar = k; }
