@@ -142,6 +142,7 @@ __device__ __forceinline__ void rev_masked(const uint32_t *prof, int R, const ui
 // Letters tp[i..i+3] from the aligned words around them: word w0 holds
 // tp's first letters at byte offset sh/8.  Reads at most 4 bytes past the
 // last letter used (the database keeps readable padding after its end).
+// Callers index with (int) letters: offsets below a row base are negative.
 struct Letters4 {
     const uint32_t *wp;
     uint32_t sh, lo;
@@ -179,10 +180,10 @@ __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint
         int i = c;
         for (; i + 4 <= ce; i += 4) {
             const uint32_t f = L4.next(i);
-            x0 += pw[(f & 0xFFu) * R - i];
-            x1 += pw[((f >> 8) & 0xFFu) * R - (i + 1)];
-            x2 += pw[((f >> 16) & 0xFFu) * R - (i + 2)];
-            x3 += pw[(f >> 24) * R - (i + 3)];
+            x0 += pw[(int)(f & 0xFFu) * R - i];
+            x1 += pw[(int)((f >> 8) & 0xFFu) * R - (i + 1)];
+            x2 += pw[(int)((f >> 16) & 0xFFu) * R - (i + 2)];
+            x3 += pw[(int)(f >> 24) * R - (i + 3)];
         }
         for (; i < ce; i++) x0 += pw[tp[i] * R - i];
         spread(x0, A);
@@ -239,10 +240,10 @@ __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uin
         int i = c;
         for (; i + 4 <= ce; i += 4) {
             const uint32_t f = L4.next(i);
-            x0 += pw[(f & 0xFFu) * R + i];
-            x1 += pw[((f >> 8) & 0xFFu) * R + (i + 1)];
-            x2 += pw[((f >> 16) & 0xFFu) * R + (i + 2)];
-            x3 += pw[(f >> 24) * R + (i + 3)];
+            x0 += pw[(int)(f & 0xFFu) * R + i];
+            x1 += pw[(int)((f >> 8) & 0xFFu) * R + (i + 1)];
+            x2 += pw[(int)((f >> 16) & 0xFFu) * R + (i + 2)];
+            x3 += pw[(int)(f >> 24) * R + (i + 3)];
         }
         for (; i < ce; i++) x0 += pw[tp[i] * R + i];
         spread(x0, A);
