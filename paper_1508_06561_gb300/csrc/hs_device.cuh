@@ -185,7 +185,10 @@ __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint
             x2 += pw[(int)((f >> 16) & 0xFFu) * R - (i + 2)];
             x3 += pw[(int)(f >> 24) * R - (i + 3)];
         }
-        for (; i < ce; i++) x0 += pw[tp[i] * R - i];
+        // tail: at most 3 iterations, one per accumulator, so none exceeds flush cells
+        if (i < ce) x0 += pw[tp[i] * R - i];
+        if (i + 1 < ce) x1 += pw[tp[i + 1] * R - (i + 1)];
+        if (i + 2 < ce) x2 += pw[tp[i + 2] * R - (i + 2)];
         spread(x0, A);
         spread(x1, A);
         spread(x2, A);
@@ -245,7 +248,10 @@ __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uin
             x2 += pw[(int)((f >> 16) & 0xFFu) * R + (i + 2)];
             x3 += pw[(int)(f >> 24) * R + (i + 3)];
         }
-        for (; i < ce; i++) x0 += pw[tp[i] * R + i];
+        // tail: at most 3 iterations, one per accumulator, so none exceeds flush cells
+        if (i < ce) x0 += pw[tp[i] * R + i];
+        if (i + 1 < ce) x1 += pw[tp[i + 1] * R + (i + 1)];
+        if (i + 2 < ce) x2 += pw[tp[i + 2] * R + (i + 2)];
         spread(x0, A);
         spread(x1, A);
         spread(x2, A);
