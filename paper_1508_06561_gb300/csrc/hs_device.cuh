@@ -139,60 +139,23 @@ __device__ __forceinline__ void rev_masked(const uint32_t *prof, int R, const ui
     spread(x, A);
 }
 
-// Letters tp[i..i+3] from the aligned words around them: word w0 holds
-// tp's first letters at byte offset sh/8.  Reads at most 4 bytes past the
-// last letter used (the database keeps readable padding after its end).
-// Callers index with (int) letters: offsets below a row base are negative.
-struct Letters4 {
-    const uint32_t *wp;
-    uint32_t sh, lo;
-    __device__ __forceinline__ void init(const uint8_t *tp)
-    {
-        const uintptr_t ad = reinterpret_cast<uintptr_t>(tp);
-        wp = reinterpret_cast<const uint32_t *>(ad & ~(uintptr_t)3);
-        sh = (uint32_t)(ad & 3) * 8;
-        lo = __ldg(wp);
-    }
-    // letters i..i+3 (i a multiple of 4, called with i = 0, 4, 8, ...)
-    __device__ __forceinline__ uint32_t next(int i)
-    {
-        const uint32_t hi = __ldg(wp + (i >> 2) + 1);
-        const uint32_t f = __funnelshift_r(lo, hi, sh);
-        lo = hi;
-        return f;
-    }
-};
-
-// Query-small main iterations p in [pa, pb): letter tl[p], word
-// pw[letter * R - (p - pa)] with pw = prof + sbase - pa.  Four accumulators,
-// each taking <= flush cells per byte between widenings.
 __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int pa,
                                          int pb, int flush, Acc4 &A)
 {
     const uint32_t *pw = prof + (sbase - pa);
     const uint8_t *tp = tl + pa;
     const int n = pb - pa;
-    Letters4 L4;
-    L4.init(tp);
-    for (int c = 0; c < n; c += 4 * flush) {
-        const int ce = min(n, c + 4 * flush);
-        uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+    for (int c = 0; c < n; c += 2 * flush) {        // x and y each take <= flush cells
+        const int ce = min(n, c + 2 * flush);
+        uint32_t x = 0, y = 0;
         int i = c;
-        for (; i + 4 <= ce; i += 4) {
-            const uint32_t f = L4.next(i);
-            x0 += pw[(int)(f & 0xFFu) * R - i];
-            x1 += pw[(int)((f >> 8) & 0xFFu) * R - (i + 1)];
-            x2 += pw[(int)((f >> 16) & 0xFFu) * R - (i + 2)];
-            x3 += pw[(int)(f >> 24) * R - (i + 3)];
+        for (; i + 1 < ce; i += 2) {
+            x += pw[tp[i] * R - i];
+            y += pw[tp[i + 1] * R - (i + 1)];
         }
-        // tail: at most 3 iterations, one per accumulator, so none exceeds flush cells
-        if (i < ce) x0 += pw[tp[i] * R - i];
-        if (i + 1 < ce) x1 += pw[tp[i + 1] * R - (i + 1)];
-        if (i + 2 < ce) x2 += pw[tp[i + 2] * R - (i + 2)];
-        spread(x0, A);
-        spread(x1, A);
-        spread(x2, A);
-        spread(x3, A);
+        if (i < ce) x += pw[tp[i] * R - i];
+        spread(x, A);
+        spread(y, A);
     }
 }
 
@@ -235,27 +198,17 @@ __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uin
     const uint32_t *pw = prof + (s0 + it0);
     const uint8_t *tp = ts + it0;
     const int n = it1 - it0;
-    Letters4 L4;
-    L4.init(tp);
-    for (int c = 0; c < n; c += 4 * flush) {
-        const int ce = min(n, c + 4 * flush);
-        uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+    for (int c = 0; c < n; c += 2 * flush) {        // x and y each take <= flush cells
+        const int ce = min(n, c + 2 * flush);
+        uint32_t x = 0, y = 0;
         int i = c;
-        for (; i + 4 <= ce; i += 4) {
-            const uint32_t f = L4.next(i);
-            x0 += pw[(int)(f & 0xFFu) * R + i];
-            x1 += pw[(int)((f >> 8) & 0xFFu) * R + (i + 1)];
-            x2 += pw[(int)((f >> 16) & 0xFFu) * R + (i + 2)];
-            x3 += pw[(int)(f >> 24) * R + (i + 3)];
+        for (; i + 1 < ce; i += 2) {
+            x += pw[tp[i] * R + i];
+            y += pw[tp[i + 1] * R + i + 1];
         }
-        // tail: at most 3 iterations, one per accumulator, so none exceeds flush cells
-        if (i < ce) x0 += pw[tp[i] * R + i];
-        if (i + 1 < ce) x1 += pw[tp[i + 1] * R + (i + 1)];
-        if (i + 2 < ce) x2 += pw[tp[i + 2] * R + (i + 2)];
-        spread(x0, A);
-        spread(x1, A);
-        spread(x2, A);
-        spread(x3, A);
+        if (i < ce) x += pw[tp[i] * R + i];
+        spread(x, A);
+        spread(y, A);
     }
 }
 
@@ -344,45 +297,11 @@ __device__ __forceinline__ void coop_scan(const uint32_t *prof, int R, int qlen,
     warp_argmax(bv, bk, vmax, kstar);
 }
 
-// The virtual score of a single shift (ls == ss): only byte 0 of each word
-// is a real cell; carries never reach it from above, so words are summed
-// and byte 0 is taken every `flush` cells.
-__device__ __forceinline__ int32_t single_shift(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
-                                                int flush)
-{
-    uint32_t v = 0;
-    if (g.qsmall) {
-        const uint32_t *pw = prof + (qlen + 3 - g.Sp);
-        const uint8_t *tp = g.t + g.Lp;
-        for (int c = 0; c < g.ss; c += flush) {
-            const int ce = min(g.ss, c + flush);
-            uint32_t x = 0;
-            for (int j = c; j < ce; j++) x += pw[tp[j] * R - j];
-            v += x & 0xFFu;
-        }
-    } else {
-        const uint32_t *pw = prof + (g.Lp + 4);
-        const uint8_t *tp = g.t + g.Sp;
-        for (int c = 0; c < g.ss; c += flush) {
-            const int ce = min(g.ss, c + flush);
-            uint32_t x = 0;
-            for (int j = c; j < ce; j++) x += pw[tp[j] * R + j];
-            v += x & 0xFFu;
-        }
-    }
-    return (int32_t)v - bias * g.ss;
-}
-
 // One lane scans a whole step alone, chunk after chunk.
 __device__ __forceinline__ void lane_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
                                           int flush, int32_t &vmax, int32_t &kstar)
 {
     const int nshift = g.ls - g.ss + 1;
-    if (nshift == 1) {
-        vmax = single_shift(prof, R, qlen, g, bias, flush);
-        kstar = 0;
-        return;
-    }
     const int32_t off = bias * g.ss;
     int32_t bv = INT_MIN, bk = INT_MAX;
     for (int k0 = 0; k0 < nshift; k0 += 4) {

@@ -169,10 +169,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
             const int64_t ssw = (int64_t)(((uint64_t)Srem * L.sf * u) >> 32);
             g.ls = ls;
             g.ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
-            // lane-local cost in loop iterations: a single shift is ss cells;
-            // otherwise every 4-shift chunk pays ~12 iterations of fixed work
-            const int64_t chunks = (ls - g.ss + 4) >> 2;
-            const int64_t iters = ls == g.ss ? (int64_t)g.ss : chunks * (g.ss + (L.qsmall ? 3 : 0) + 12);
+            const int64_t iters = (int64_t)((ls - g.ss + 4) >> 2) * (g.ss + (L.qsmall ? 3 : 0));
             local = iters <= kLocalIters;
             if (local) {
                 lane_scan(prof + (L.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, g, kp.bias, kp.flush,

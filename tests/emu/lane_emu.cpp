@@ -1,0 +1,93 @@
+// Host check of the scan's per-lane arithmetic (compiled with g++ against
+// the stub cuda_runtime.h next to this file).  Random queries, targets,
+// matrices and step windows; every 4-shift chunk sum, split into random
+// segments, and every lane-local step must equal a naive sum of matrix
+// entries, and every profile/target read must stay inside its buffer: the
+// buffers end at PROT_NONE guard pages, so a stray read faults.
+// usage: lane_emu SEED [MIN MAX]   (matrix entries drawn from [MIN, MAX])
+#include <sys/mman.h>
+#include <unistd.h>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <random>
+#include "hs_device.cuh"
+using namespace hs;
+// buffer with PROT_NONE guard pages on both sides; data placed flush against the tail guard
+template <class T> T *guarded(size_t n, T **base_out) {
+    size_t pg = sysconf(_SC_PAGESIZE);
+    size_t bytes = n * sizeof(T);
+    size_t body = (bytes + pg - 1) / pg * pg;
+    char *m = (char *)mmap(nullptr, body + 2 * pg, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    mprotect(m, pg, PROT_NONE);
+    mprotect(m + pg + body, pg, PROT_NONE);
+    T *p = (T *)(m + pg + body - bytes);      // end of data touches the guard
+    *base_out = p;
+    return p;
+}
+int main(int argc, char **argv) {
+    std::mt19937_64 rng(argc > 1 ? atoi(argv[1]) : 1);
+    int8_t M[576];
+    int mlo = argc > 2 ? atoi(argv[2]) : -4, mhi = argc > 3 ? atoi(argv[3]) : 11;
+    for (int a = 0; a < 24; a++) for (int b = 0; b <= a; b++) { int v = mlo + (int)(rng() % (mhi - mlo + 1)); M[a*24+b] = M[b*24+a] = (int8_t)v; }
+    int lo = 127, hi = -128; for (int i = 0; i < 576; i++) { lo = std::min<int>(lo, M[i]); hi = std::max<int>(hi, M[i]); }
+    int bias = -lo, flush = hi == lo ? 255 : std::max(1, 255 / (hi - lo));
+    long checks = 0;
+    for (int trial = 0; trial < 3000; trial++) {
+        int qlen = 1 + rng() % 300;
+        int tlen = 1 + rng() % 600;
+        std::vector<uint8_t> q(qlen);
+        for (auto &c : q) c = rng() % 24;
+        // database: the target, then 64 pad bytes (as the library allocates)
+        uint8_t *tb; uint8_t *t = guarded<uint8_t>(tlen + kCodesPad, &tb);
+        for (int i = 0; i < tlen; i++) t[i] = rng() % 24;
+        memset(t + tlen, 0, kCodesPad);
+        int R = profile_stride(qlen);
+        for (int rev = 0; rev < 2; rev++) {
+            uint32_t *pb; uint32_t *prof = guarded<uint32_t>((size_t)profile_words(qlen), &pb);
+            for (int a = 0; a < 24; a++) for (int s = 0; s < R; s++) prof[a * R + s] = profile_word_value(q.data(), qlen, rev, M, bias, a, s);
+            bool qsmall = rev;   // rev profile <-> query small
+            int nl = qsmall ? tlen : qlen, ns = qsmall ? qlen : tlen;
+            const uint8_t *L = qsmall ? t : q.data(), *S = qsmall ? q.data() : t;
+            // random step windows
+            for (int w = 0; w < 20; w++) {
+                int Lp = rng() % nl, Sp = rng() % ns;
+                int Lrem = nl - Lp, Srem = ns - Sp;
+                int ls = 1 + rng() % Lrem;
+                int ss = 1 + rng() % std::min(Srem, ls);
+                Plan g = {t, Lp, Sp, ls, ss, qsmall ? 1 : 0, 0, 0, 0};
+                int nshift = ls - ss + 1;
+                // naive
+                int bestv = INT32_MIN, bestk = 0;
+                std::vector<int> V(nshift);
+                for (int k = 0; k < nshift; k++) { int v = 0; for (int j = 0; j < ss; j++) { int a = L[Lp+k+j], b = S[Sp+j]; v += qsmall ? M[b*24+a] : M[a*24+b]; } V[k] = v; if (v > bestv) { bestv = v; bestk = k; } }
+                // lane scan (whole step) and per-chunk segments with random splits
+                int32_t vm, ks;
+                if (nshift <= 64) {
+                    lane_scan(prof, R, qlen, g, bias, flush, vm, ks);
+                    if (vm != bestv || ks != bestk) { printf("lane_scan mismatch trial %d\n", trial); return 1; }
+                }
+                int niter = qsmall ? ss + 3 : ss;
+                for (int k0 = 0; k0 < nshift; k0 += 4) {
+                    int nseg = 1 + rng() % 4;
+                    int minseg = qsmall ? 6 : 4;
+                    if (niter < nseg * minseg) nseg = 1;
+                    Acc4 A = {0, 0, 0, 0};
+                    for (int sg = 0; sg < nseg; sg++) {
+                        int it0 = sg * niter / nseg, it1 = (sg + 1) * niter / nseg;
+                        if (qsmall) rev_segment(prof, R, t + Lp + k0, qlen + 3 - Sp, ss, it0, it1, sg == 0, sg == nseg - 1, flush, A);
+                        else fwd_chunk(prof, R, t + Sp, Lp + k0 + 4, it0, it1, flush, A);
+                    }
+                    uint32_t acc[4] = {A.a0, A.a1, A.a2, A.a3};
+                    for (int x = 0; x < 4 && k0 + x < nshift; x++) {
+                        if ((int)acc[x] - bias * ss != V[k0 + x]) { printf("chunk mismatch trial %d k %d\n", trial, k0 + x); return 1; }
+                        checks++;
+                    }
+                }
+            }
+        }
+    }
+    printf("emu ok: %ld shift sums checked\n", checks);
+    return 0;
+}
