@@ -111,6 +111,18 @@ int hs_params_check(const hs_params *p);
 int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs,
                void *stream, hs_db **out);
 
+/* A database shard: the same as hs_db_load for sequences whose global
+ * database indices start at index_base (>= 0).  Draws, ties and reported
+ * hit indices use global indices, so the shards of a database searched
+ * separately and merged by (score desc, index asc) give exactly the hits of
+ * the whole database (the sharded search of the design notes, Sec. III.B.3
+ * applied per shard). */
+int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, int64_t index_base,
+                     void *stream, hs_db **out);
+
+/* The global index of a database's first sequence (0 unless a shard). */
+int hs_db_index_base(const hs_db *db, int64_t *index_base);
+
 /* Number of sequences, residues and the longest length of a database. */
 int hs_db_info(const hs_db *db, int64_t *n_seqs, int64_t *n_residues, int32_t *max_len);
 
@@ -182,9 +194,63 @@ int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
               hs_hit *hits_out, int32_t *n_hits_out,
               uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used);
 
+/* Batched search: nq queries against the resident database in one
+ * persistent scan launch (profiles of all queries, then (query, chunk) work
+ * items over the length order, then every query's top k and alignments).
+ * Each query's result is exactly hs_search's for that query and its seed.
+ * Queries are concatenated: query i is queries[qoffsets[i] .. qoffsets[i+1]).
+ * Hits of query i occupy hits[i*k .. i*k + min(k, n_seqs)); their ops
+ * offsets index one ops buffer shared by all queries.
+ * tuning (optional, NULL = defaults): chunks = work items per query over the
+ * database (<= 8192; default 1024), ctas_per_sm = resident CTAs per SM
+ * (0 = as many as fit).  Results never depend on the tuning. */
+typedef struct {
+    int32_t chunks;
+    int32_t ctas_per_sm;
+} hs_batch_tuning;
+
+/* Workspace for hs_search_batch_device (total_qlen = sum of query lengths,
+ * max_qlen = the longest). */
+int hs_search_batch_workspace_size(const hs_db *db, int32_t nq, int64_t total_qlen, int32_t max_qlen,
+                                   int32_t k, size_t *bytes);
+
+/* Ops capacity (entries) that always suffices for a batch. */
+int64_t hs_batch_ops_capacity(int32_t nq, int64_t total_qlen, int32_t k);
+
+/* Device-resident batched search, asynchronous on `stream` (no host copies,
+ * no allocation, so it can be captured in a CUDA graph by the caller).
+ *   d_queries, d_qoffsets (int64[nq+1]), d_seeds (uint64[nq]): device; the
+ *   offsets must describe queries of 1..max_qlen letters totalling
+ *   total_qlen (the host cannot check device data).
+ *   d_hits: nq*k records; d_ops/ops_cap/d_ops_used/d_status as for
+ *   hs_search_device. */
+int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries, const int64_t *d_qoffsets,
+                           const uint64_t *d_seeds, int64_t total_qlen, int32_t max_qlen,
+                           const hs_params *p, int32_t k, const hs_batch_tuning *tuning, void *stream,
+                           void *d_workspace, size_t ws_bytes, hs_hit *d_hits, uint32_t *d_ops,
+                           int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status);
+
+/* The same from host buffers (queries, qoffsets, seeds, hits_out with room
+ * for nq*k records); *n_hits_out = min(k, n_seqs) per query. */
+int hs_search_batch(hs_db *db, int32_t nq, const uint8_t *queries, const int64_t *qoffsets,
+                    const uint64_t *seeds, const hs_params *p, int32_t k, const hs_batch_tuning *tuning,
+                    void *stream, hs_hit *hits_out, int32_t *n_hits_out, uint32_t *ops_out,
+                    int64_t ops_cap, int64_t *ops_used);
+
+/* Threshold reporting (Sec. IV: hits "with appropriately set threshold
+ * score").  The same search as hs_search, keeping every pair that scores
+ * >= threshold, ranked, at most max_hits (<= HS_MAX_K) of them with their
+ * alignments.  *n_above_out receives the number of pairs at or above the
+ * threshold (more than *n_hits_out when max_hits truncated the list). */
+int hs_search_threshold(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
+                        int32_t threshold, int32_t max_hits, uint64_t seed, void *stream,
+                        hs_hit *hits_out, int32_t *n_hits_out, int64_t *n_above_out,
+                        uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used);
+
 /* One pair replayed alone (Fig. 1's AlignSequences for the query and
  * database sequence db_index, with the same draws as hs_search): its score
- * and its alignment ops (host buffer of `cap` entries). */
+ * and its alignment ops (host buffer of `cap` entries).  db_index is the
+ * global index (as reported in hits; shards subtract their index base). */
 int hs_get_alignment(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
                      uint64_t seed, int64_t db_index, void *stream,
                      uint32_t *ops_out, int64_t cap, int32_t *score_out,

@@ -21,7 +21,9 @@ import numpy as np
 from . import _lib
 from ._lib import HIT_DTYPE, HS_OP_D, HS_OP_I, HS_OP_M, HsError, check, lib
 
-__all__ = ["Params", "Database", "search", "search_device", "search_device_noalloc", "get_alignment", "encode",
+__all__ = ["Params", "Database", "search", "search_threshold", "search_batch", "search_batch_device",
+           "search_device", "search_device_noalloc",
+           "get_alignment", "encode",
            "builtin_matrix", "ops_to_rows", "HIT_DTYPE", "HsError", "workspace_size"]
 
 GAP = 0xFF
@@ -75,14 +77,18 @@ def _stream_ptr(stream):
 
 
 class Database:
-    """A database resident on the current CUDA device (hs_db_load)."""
+    """A database resident on the current CUDA device (hs_db_load).  With
+    index_base > 0 it is a shard whose first sequence has that global index
+    (hs_db_load_shard): hits report, and draws use, global indices."""
 
-    def __init__(self, codes, offsets, stream=None):
+    def __init__(self, codes, offsets, stream=None, index_base: int = 0):
         codes = np.ascontiguousarray(codes, dtype=np.uint8)
         offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         h = C.c_void_p()
-        check(lib().hs_db_load(codes.ctypes.data if len(codes) else None, offsets.ctypes.data,
-                               len(offsets) - 1, _stream_ptr(stream), C.byref(h)), "hs_db_load")
+        check(lib().hs_db_load_shard(codes.ctypes.data if len(codes) else None, offsets.ctypes.data,
+                                     len(offsets) - 1, index_base, _stream_ptr(stream), C.byref(h)),
+              "hs_db_load_shard")
+        self.index_base = index_base
         self._h = h
         n, r, m = C.c_int64(), C.c_int64(), C.c_int32()
         check(lib().hs_db_info(h, C.byref(n), C.byref(r), C.byref(m)), "hs_db_info")
@@ -125,6 +131,104 @@ def search(db: Database, query, k: int, params: Params | None = None, seed: int 
                           _stream_ptr(stream), hits.ctypes.data, C.byref(n_out), ops.ctypes.data,
                           cap, C.byref(used)), "hs_search")
     return hits[:n_out.value].copy(), ops[:used.value].copy()
+
+
+def search_threshold(db: Database, query, threshold: int, max_hits: int, params: Params | None = None,
+                     seed: int = 0, stream=None):
+    """hs_search_threshold: every pair scoring >= threshold (at most
+    max_hits, ranked) -> (hits, ops, number of pairs at or above)."""
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    p, _keep = (params or Params()).to_c()
+    nh = min(max_hits, db.n)
+    hits = np.zeros(max(nh, 1), HIT_DTYPE)
+    cap = lib().hs_ops_capacity(len(q), max_hits)
+    ops = np.zeros(max(cap, 1), np.uint32)
+    n_out, above, used = C.c_int32(), C.c_int64(), C.c_int64()
+    check(lib().hs_search_threshold(db.handle, q.ctypes.data, len(q), C.byref(p), threshold, max_hits,
+                                    seed & (2**64 - 1), _stream_ptr(stream), hits.ctypes.data, C.byref(n_out),
+                                    C.byref(above), ops.ctypes.data, cap, C.byref(used)), "hs_search_threshold")
+    return hits[:n_out.value].copy(), ops[:used.value].copy(), int(above.value)
+
+
+def _tuning(tuning):
+    if tuning is None:
+        return None
+    if isinstance(tuning, _lib.hs_batch_tuning):
+        return tuning
+    return _lib.hs_batch_tuning(int(tuning.get("chunks", 0)), int(tuning.get("ctas_per_sm", 0)))
+
+
+def _pack_queries(queries):
+    qs = [np.ascontiguousarray(q, dtype=np.uint8) for q in queries]
+    off = np.zeros(len(qs) + 1, np.int64)
+    np.cumsum([len(q) for q in qs], out=off[1:])
+    cat = np.concatenate(qs) if qs else np.zeros(0, np.uint8)
+    return cat, off
+
+
+def search_batch(db: Database, queries, k: int, params: Params | None = None, seeds=None, tuning=None,
+                 stream=None):
+    """hs_search_batch: many queries in one scan launch.  Returns a list of
+    (hits, ops) per query, each exactly what search() gives for that query
+    and its seed (seeds default to 0).  tuning: {"chunks", "ctas_per_sm"}."""
+    cat, off = _pack_queries(queries)
+    nq = len(off) - 1
+    sd = np.zeros(nq, np.uint64) if seeds is None else np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    p, _keep = (params or Params()).to_c()
+    hits = np.zeros(max(nq * k, 1), HIT_DTYPE)
+    cap = lib().hs_batch_ops_capacity(nq, int(off[-1]), k)
+    ops = np.zeros(max(cap, 1), np.uint32)
+    n_out, used = C.c_int32(), C.c_int64()
+    t = _tuning(tuning)
+    check(lib().hs_search_batch(db.handle, nq, cat.ctypes.data, off.ctypes.data, sd.ctypes.data, C.byref(p), k,
+                                C.byref(t) if t is not None else None, _stream_ptr(stream), hits.ctypes.data,
+                                C.byref(n_out), ops.ctypes.data, cap, C.byref(used)), "hs_search_batch")
+    nh = n_out.value
+    out = []
+    for i in range(nq):
+        h = hits[i * k:i * k + nh].copy()
+        segs = [ops[x["ops_offset"]:x["ops_offset"] + x["ops_len"]] for x in h]
+        o = np.concatenate(segs).astype(np.uint32) if segs else np.zeros(0, np.uint32)
+        pos = 0
+        for j in range(len(h)):
+            h[j]["ops_offset"] = pos
+            pos += h[j]["ops_len"]
+        out.append((h, o))
+    return out
+
+
+def search_batch_device(db: Database, queries_cat, qoffsets, seeds, max_qlen: int, k: int,
+                        params: Params | None = None, tuning=None, stream=None, workspace=None, out=None):
+    """hs_search_batch_device with torch CUDA tensors (queries_cat uint8,
+    qoffsets int64[nq+1], seeds int64/uint64[nq]); asynchronous."""
+    import torch
+    dev = queries_cat.device
+    nq = int(qoffsets.numel()) - 1
+    total = int(queries_cat.numel())
+    b = C.c_size_t()
+    check(lib().hs_search_batch_workspace_size(db.handle, nq, total, max_qlen, k, C.byref(b)),
+          "hs_search_batch_workspace_size")
+    if workspace is None or workspace.numel() < b.value:
+        workspace = torch.empty(b.value, dtype=torch.uint8, device=dev)
+    cap = lib().hs_batch_ops_capacity(nq, total, k)
+    if out is None:
+        out = {"hits": torch.empty(max(nq * k, 1) * HIT_DTYPE.itemsize, dtype=torch.uint8, device=dev),
+               "ops": torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+               "ops_used": torch.zeros(1, dtype=torch.int64, device=dev),
+               "status": torch.zeros(1, dtype=torch.int32, device=dev)}
+    out["workspace"] = workspace
+    p, _keep = (params or Params()).to_c()
+    t = _tuning(tuning)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    check(lib().hs_search_batch_device(db.handle, nq, queries_cat.data_ptr(), qoffsets.data_ptr(), seeds.data_ptr(),
+                                       total, max_qlen, C.byref(p), k, C.byref(t) if t is not None else None,
+                                       _stream_ptr(st), workspace.data_ptr(), b.value, out["hits"].data_ptr(),
+                                       out["ops"].data_ptr(), cap, out["ops_used"].data_ptr(),
+                                       out["status"].data_ptr()), "hs_search_batch_device")
+    out["n_hits"] = min(k, db.n)
+    out["nq"] = nq
+    out["k"] = k
+    return out
 
 
 def search_device(db: Database, query, k: int, params: Params | None = None, seed: int = 0,

@@ -30,6 +30,10 @@ class hs_trace(C.Structure):
     _fields_ = [("scan_start", C.c_void_p), ("scan_stop", C.c_void_p), ("launches", C.c_int32)]
 
 
+class hs_batch_tuning(C.Structure):
+    _fields_ = [("chunks", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
 class HsError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = status
@@ -58,6 +62,9 @@ def lib():
     L.hs_params_check.argtypes = [P(hs_params)]
     L.hs_db_load.argtypes = [vp, vp, i64, vp, P(vp)]
     L.hs_db_info.argtypes = [vp, P(i64), P(i64), P(i32)]
+    L.hs_db_load_shard.argtypes = [vp, vp, i64, i64, vp, P(vp)]
+    L.hs_db_index_base.argtypes = [vp, P(i64)]
+    L.hs_search_threshold.argtypes = [vp, vp, i32, P(hs_params), i32, i32, u64, vp, vp, P(i32), P(i64), vp, i64, P(i64)]
     L.hs_db_free.argtypes = [vp]
     L.hs_db_free.restype = None
     L.hs_search_workspace_size.argtypes = [vp, i32, i32, P(sz)]
@@ -68,12 +75,21 @@ def lib():
     L.hs_get_alignment.argtypes = [vp, vp, i32, P(hs_params), u64, i64, vp, vp, i64, P(i32), P(i64), vp]
     L.hs_search_device_noalloc.argtypes = [vp, vp, i32, P(hs_params), i32, u64, vp, vp, vp, i64, vp, vp, vp, vp]
     L.hs_search_transfer_bytes.argtypes = [i32, i32, P(i64), P(i64)]
+    L.hs_search_batch_workspace_size.argtypes = [vp, i32, i64, i32, i32, P(sz)]
+    L.hs_batch_ops_capacity.argtypes = [i32, i64, i32]
+    L.hs_batch_ops_capacity.restype = i64
+    L.hs_search_batch_device.argtypes = [vp, i32, vp, vp, vp, i64, i32, P(hs_params), i32, P(hs_batch_tuning), vp,
+                                         vp, sz, vp, vp, i64, vp, vp]
+    L.hs_search_batch.argtypes = [vp, i32, vp, vp, vp, P(hs_params), i32, P(hs_batch_tuning), vp, vp, P(i32), vp,
+                                  i64, P(i64)]
     L.hs_db_set_trace.argtypes = [vp, P(hs_trace)]
     L.hs_strerror.argtypes = [C.c_int]
     L.hs_strerror.restype = C.c_char_p
     for name in ("hs_encode", "hs_builtin_matrix", "hs_params_check", "hs_db_load", "hs_db_info",
                  "hs_search_workspace_size", "hs_search_device", "hs_search", "hs_get_alignment",
-                 "hs_search_transfer_bytes", "hs_db_set_trace", "hs_search_device_noalloc"):
+                 "hs_search_transfer_bytes", "hs_db_set_trace", "hs_search_device_noalloc",
+                 "hs_db_load_shard", "hs_db_index_base", "hs_search_threshold",
+                 "hs_search_batch_workspace_size", "hs_search_batch_device", "hs_search_batch"):
         getattr(L, name).restype = C.c_int
     _L = L
     return L

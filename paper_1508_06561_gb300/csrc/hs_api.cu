@@ -101,13 +101,16 @@ static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams
         lo = std::min<int>(lo, m[i]);
         hi = std::max<int>(hi, m[i]);
     }
-    kp->bias = -lo;
+    SParams &sp = kp->s;
+    sp.bias = -lo;
     const int range = hi - lo;
-    kp->flush = range == 0 ? 255 : std::max(1, 255 / range);
-    kp->pgp = p->pgp; kp->gop = p->gop; kp->gep = p->gep; kp->rounds = p->rounds;
-    kp->lf_q16 = p->lfactor_q16; kp->sf_q16 = p->sfactor_q16; kp->minf_q16 = p->minfactor_q16;
-    kp->qlen = qlen;
-    kp->seed = seed;
+    sp.flush = range == 0 ? 255 : std::max(1, 255 / range);
+    sp.pgp = p->pgp; sp.gop = p->gop; sp.gep = p->gep; sp.rounds = p->rounds;
+    sp.lf_q16 = p->lfactor_q16; sp.sf_q16 = p->sfactor_q16; sp.minf_q16 = p->minfactor_q16;
+    sp.qlen = qlen;
+    sp.seed = seed;
+    sp.index_base = 0;
+    sp.min_score = INT_MIN;
     return HS_OK;
 }
 
@@ -117,11 +120,13 @@ using namespace hs;
 
 struct hs_db {
     int64_t n = 0, nres = 0;
+    int64_t index_base = 0;                 // global index of sequence 0 (database shards)
     int32_t maxlen = 0;
     int device = 0, num_sms = 0;
     uint8_t *d_codes = nullptr;
     int64_t *d_offsets = nullptr;
     int32_t *d_order = nullptr;
+    int64_t *d_cumres = nullptr;            // residues before each position of the length order
     std::vector<int32_t> sorted_len;        // lengths in scheduling order (non-increasing)
     // host-API state (grown on demand)
     void *d_ws = nullptr;
@@ -201,6 +206,7 @@ void hs_db_free(hs_db *db)
     cudaFree(db->d_codes);
     cudaFree(db->d_offsets);
     cudaFree(db->d_order);
+    cudaFree(db->d_cumres);
     cudaFree(db->d_ws);
     cudaFree(db->d_io);
     if (db->h_io) cudaFreeHost(db->h_io);
@@ -209,6 +215,13 @@ void hs_db_free(hs_db *db)
 
 int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, void *stream, hs_db **out)
 {
+    return hs_db_load_shard(codes, offsets, n_seqs, 0, stream, out);
+}
+
+int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, int64_t index_base,
+                     void *stream, hs_db **out)
+{
+    if (index_base < 0 || index_base > (int64_t)INT32_MAX) return HS_EINVAL;
     if (!out || !offsets || n_seqs < 0 || n_seqs > INT32_MAX - 1) return HS_EINVAL;
     *out = nullptr;
     if (offsets[0] != 0) return HS_EINVAL;
@@ -229,6 +242,7 @@ int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, voi
     db->n = n_seqs;
     db->nres = nres;
     db->maxlen = maxlen;
+    db->index_base = index_base;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaGetDevice(&db->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->device);
@@ -241,7 +255,11 @@ int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, voi
         return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
     });
     db->sorted_len.resize((size_t)n_seqs);
-    for (int64_t i = 0; i < n_seqs; i++) db->sorted_len[i] = (int32_t)(offsets[order[i] + 1] - offsets[order[i]]);
+    std::vector<int64_t> cumres((size_t)n_seqs + 1, 0);
+    for (int64_t i = 0; i < n_seqs; i++) {
+        db->sorted_len[i] = (int32_t)(offsets[order[i] + 1] - offsets[order[i]]);
+        cumres[i + 1] = cumres[i] + db->sorted_len[i];
+    }
 
     e = cudaMalloc(&db->d_codes, (size_t)nres + kCodesPad);
     if (e == cudaSuccess) e = cudaMalloc(&db->d_offsets, sizeof(int64_t) * (size_t)(n_seqs + 1));
@@ -250,9 +268,18 @@ int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, voi
     if (e == cudaSuccess && nres > 0) e = cudaMemcpyAsync(db->d_codes, codes, (size_t)nres, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_offsets, offsets, sizeof(int64_t) * (size_t)(n_seqs + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && n_seqs > 0) e = cudaMemcpyAsync(db->d_order, order.data(), sizeof(int32_t) * (size_t)n_seqs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc(&db->d_cumres, sizeof(int64_t) * (size_t)(n_seqs + 1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_cumres, cumres.data(), sizeof(int64_t) * (size_t)(n_seqs + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { hs_db_free(db); return from_cuda(e); }
     *out = db;
+    return HS_OK;
+}
+
+int hs_db_index_base(const hs_db *db, int64_t *index_base)
+{
+    if (!db || !index_base) return HS_EINVAL;
+    *index_base = db->index_base;
     return HS_OK;
 }
 
@@ -280,10 +307,12 @@ int64_t hs_ops_capacity(int32_t qlen, int32_t k)
     return (int64_t)k * slot_stride_for(qlen);
 }
 
-int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, const hs_params *p, int32_t k,
-                     uint64_t seed, void *stream, void *d_workspace, size_t ws_bytes, hs_hit *d_hits,
-                     uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used, int32_t *d_scores,
-                     int64_t *d_cells, int32_t *d_status)
+// The search pipeline on the device: profile -> scan -> top-k -> replay,
+// plus (threshold search) the count of pairs scoring >= min_score.
+static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, const hs_params *p, int32_t k,
+                      uint64_t seed, int32_t min_score, void *stream, void *d_workspace, size_t ws_bytes,
+                      hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used, int32_t *d_scores,
+                      int64_t *d_cells, int32_t *d_status, int64_t *d_count)
 {
     if (!db || !d_query || !p || !d_workspace || !d_status) return HS_EINVAL;
     if (qlen < 1) return HS_EINVAL;
@@ -296,6 +325,8 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, cons
     KParams kp;
     int rc = make_kparams(p, qlen, seed, &kp);
     if (rc != HS_OK) return rc;
+    kp.s.index_base = db->index_base;
+    kp.s.min_score = min_score;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Workspace ws = carve_workspace(d_workspace, db->n, qlen, k);
@@ -305,6 +336,10 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, cons
     if (e != cudaSuccess) return from_cuda(e);
     if (nhits == 0 && d_ops_used) {
         e = cudaMemsetAsync(d_ops_used, 0, sizeof(int64_t), st);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (d_count) {
+        e = cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
         if (e != cudaSuccess) return from_cuda(e);
     }
     if (db->n == 0) return HS_OK;
@@ -322,12 +357,23 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, cons
     int launches = 0;
     e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st, db->trace ? &tr : nullptr,
                     &launches);
+    if (e == cudaSuccess && d_count)
+        e = launch_count_at_least(ws.scores, db->n, min_score, d_count, db->num_sms, st, &launches);
     if (e == cudaSuccess && nhits > 0) e = launch_topk(ws, db->n, nhits, st, &launches);
     if (e == cudaSuccess && nhits > 0)
         e = launch_replay(v, d_query, kp, ws, nhits, d_hits, d_ops, ops_cap, d_ops_used, d_status, st,
                           &launches);
     if (db->trace) db->trace->launches = launches;
     return from_cuda(e);
+}
+
+int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, const hs_params *p, int32_t k,
+                     uint64_t seed, void *stream, void *d_workspace, size_t ws_bytes, hs_hit *d_hits,
+                     uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used, int32_t *d_scores,
+                     int64_t *d_cells, int32_t *d_status)
+{
+    return run_search(db, d_query, qlen, p, k, seed, INT_MIN, stream, d_workspace, ws_bytes, d_hits, d_ops,
+                      ops_cap, d_ops_used, d_scores, d_cells, d_status, nullptr);
 }
 
 // host-API buffers: [query | hits | ops_used, status | ops]
@@ -391,9 +437,13 @@ int hs_db_set_trace(hs_db *db, hs_trace *trace)
     return HS_OK;
 }
 
-int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p, int32_t k, uint64_t seed,
-              void *stream, hs_hit *hits_out, int32_t *n_hits_out, uint32_t *ops_out, int64_t ops_cap,
-              int64_t *ops_used)
+// Host-buffer search (query in, hits and ops out, synchronised); with a
+// threshold, only hits scoring >= min_score are kept and *n_above receives
+// the number of pairs at or above it.
+static int run_host_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p, int32_t k,
+                           uint64_t seed, int32_t min_score, bool threshold, void *stream, hs_hit *hits_out,
+                           int32_t *n_hits_out, uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used,
+                           int64_t *n_above)
 {
     if (!db || !query || !p || !n_hits_out || !ops_used) return HS_EINVAL;
     if (qlen < 1) return HS_EINVAL;
@@ -415,26 +465,229 @@ int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
     cudaError_t e = cudaMemcpyAsync(d + l.q, h + l.q, (size_t)qlen, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
     const int64_t cap = hs_ops_capacity(qlen, k);
-    rc = hs_search_device(db, reinterpret_cast<const uint8_t *>(d + l.q), qlen, p, k, seed, stream, db->d_ws,
-                          db->ws_bytes, reinterpret_cast<hs_hit *>(d + l.hits), reinterpret_cast<uint32_t *>(d + l.ops),
-                          cap, reinterpret_cast<int64_t *>(d + l.meta), nullptr, nullptr,
-                          reinterpret_cast<int32_t *>(d + l.meta + 8));
+    rc = run_search(db, reinterpret_cast<const uint8_t *>(d + l.q), qlen, p, k, seed, min_score, stream, db->d_ws,
+                    db->ws_bytes, reinterpret_cast<hs_hit *>(d + l.hits), reinterpret_cast<uint32_t *>(d + l.ops),
+                    cap, reinterpret_cast<int64_t *>(d + l.meta), nullptr, nullptr,
+                    reinterpret_cast<int32_t *>(d + l.meta + 8),
+                    threshold ? reinterpret_cast<int64_t *>(d + l.meta + 16) : nullptr);
     if (rc != HS_OK) return rc;
-    // one copy back: hits, ops_used/status and the packed ops
+    // one copy back: hits, ops_used/status/count and the packed ops
     e = cudaMemcpyAsync(h + l.hits, d + l.hits, l.total - l.hits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    int64_t used, count = 0;
+    int32_t status;
+    std::memcpy(&used, h + l.meta, sizeof(used));
+    std::memcpy(&status, h + l.meta + 8, sizeof(status));
+    if (threshold) std::memcpy(&count, h + l.meta + 16, sizeof(count));
+    if (nhits == 0) used = 0;
+    if (status != HS_OK) return status;
+    const hs_hit *dh = reinterpret_cast<const hs_hit *>(h + l.hits);
+    int32_t keep = nhits;
+    if (threshold) {                        // hits are ranked: keep the prefix above the threshold
+        keep = 0;
+        while (keep < nhits && dh[keep].score >= min_score) keep++;
+        *n_above = count;
+    }
+    if (keep > 0) std::memcpy(hits_out, dh, sizeof(hs_hit) * (size_t)keep);
+    *n_hits_out = keep;
+    *ops_used = used;
+    if (used > ops_cap) return HS_ETRUNC;
+    if (used > 0) std::memcpy(ops_out, h + l.ops, sizeof(uint32_t) * (size_t)used);
+    return HS_OK;
+}
+
+int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p, int32_t k, uint64_t seed,
+              void *stream, hs_hit *hits_out, int32_t *n_hits_out, uint32_t *ops_out, int64_t ops_cap,
+              int64_t *ops_used)
+{
+    return run_host_search(db, query, qlen, p, k, seed, INT_MIN, false, stream, hits_out, n_hits_out, ops_out,
+                           ops_cap, ops_used, nullptr);
+}
+
+int hs_search_threshold(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p, int32_t threshold,
+                        int32_t max_hits, uint64_t seed, void *stream, hs_hit *hits_out, int32_t *n_hits_out,
+                        int64_t *n_above_out, uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used)
+{
+    if (!n_above_out) return HS_EINVAL;
+    return run_host_search(db, query, qlen, p, max_hits, seed, threshold, true, stream, hits_out, n_hits_out,
+                           ops_out, ops_cap, ops_used, n_above_out);
+}
+
+// ---------------------------------------------------------------------------
+// Batched search: many queries, one persistent scan launch.
+// ---------------------------------------------------------------------------
+static size_t batch_layout(int64_t n, int32_t nq, int64_t total_qlen, int32_t max_qlen, int32_t k, char *base,
+                           BatchLayout *bl)
+{
+    char *p = base;
+    size_t used = 0;
+    auto take = [&](size_t bytes) {
+        char *r = p ? p + used : nullptr;
+        used += align256(bytes);
+        return r;
+    };
+    const size_t kk = (size_t)std::max(k, 1), qq = (size_t)std::max(nq, 1);
+    BatchLayout b = {};
+    b.counter_bytes = (int64_t)(sizeof(unsigned) * (2 + qq));
+    b.counters = reinterpret_cast<unsigned *>(take((size_t)b.counter_bytes));
+    b.prof_off = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * qq));
+    b.prof = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 2 * kNSym * (size_t)(total_qlen + 17 * qq)));
+    b.bounds = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (kMaxChunks + 1)));
+    b.scores = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * qq * (size_t)std::max<int64_t>(n, 1)));
+    b.cand = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * qq * kTopkCtas * kk));
+    b.hit_idx = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * qq * kk));
+    b.hit_score = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * qq * kk));
+    b.slot_stride = slot_stride_for(std::max(max_qlen, 1));
+    b.slots = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * qq * kk * (size_t)b.slot_stride));
+    b.slot_len = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * qq * kk));
+    if (b.counters) {
+        b.item_ctr = b.counters;
+        b.replay_ticket = b.counters + 1;
+        b.topk_tickets = b.counters + 2;
+    }
+    b.nq = nq;
+    b.max_qlen = max_qlen;
+    if (bl) *bl = b;
+    return used;
+}
+
+int hs_search_batch_workspace_size(const hs_db *db, int32_t nq, int64_t total_qlen, int32_t max_qlen, int32_t k,
+                                   size_t *bytes)
+{
+    if (!db || !bytes || nq < 0 || total_qlen < 0 || max_qlen < 1 || k < 0 || k > HS_MAX_K) return HS_EINVAL;
+    if (max_qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    *bytes = batch_layout(db->n, nq, total_qlen, max_qlen, k, nullptr, nullptr);
+    return HS_OK;
+}
+
+int64_t hs_batch_ops_capacity(int32_t nq, int64_t total_qlen, int32_t k)
+{
+    if (nq < 0 || total_qlen < 0 || k < 0) return 0;
+    return (int64_t)k * (2 * total_qlen + 4LL * nq);
+}
+
+int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries, const int64_t *d_qoffsets,
+                           const uint64_t *d_seeds, int64_t total_qlen, int32_t max_qlen, const hs_params *p,
+                           int32_t k, const hs_batch_tuning *tuning, void *stream, void *d_workspace,
+                           size_t ws_bytes, hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap,
+                           int64_t *d_ops_used, int32_t *d_status)
+{
+    if (!db || !p || !d_workspace || !d_status || nq < 0) return HS_EINVAL;
+    if (nq > 0 && (!d_queries || !d_qoffsets || !d_seeds)) return HS_EINVAL;
+    if (max_qlen < 1 || total_qlen < nq) return HS_EINVAL;
+    if (max_qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    if (k < 0 || k > HS_MAX_K || ops_cap < 0) return HS_EINVAL;
+    const int32_t nchunk = tuning && tuning->chunks > 0 ? tuning->chunks : kDefaultChunks;
+    if (nchunk > kMaxChunks) return HS_EINVAL;
+    const int ctas_per_sm = tuning ? tuning->ctas_per_sm : 0;
+    const int32_t nhits = (int32_t)std::min<int64_t>(k, db->n);
+    if (nhits > 0 && nq > 0 && (!d_hits || !d_ops_used || (ops_cap > 0 && !d_ops))) return HS_EINVAL;
+    if (((uintptr_t)d_workspace & 255) != 0) return HS_EINVAL;
+    BatchLayout bl;
+    const size_t need = batch_layout(db->n, nq, total_qlen, max_qlen, k, static_cast<char *>(d_workspace), &bl);
+    if (ws_bytes < need) return HS_ETRUNC;
+    KParams kp;
+    int rc = make_kparams(p, max_qlen, 0, &kp);
+    if (rc != HS_OK) return rc;
+    kp.s.index_base = db->index_base;
+    bl.queries = d_queries;
+    bl.qoffsets = d_qoffsets;
+    bl.seeds = d_seeds;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(bl.counters, 0, (size_t)bl.counter_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess && d_ops_used) e = cudaMemsetAsync(d_ops_used, 0, sizeof(int64_t), st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (db->n == 0 || nq == 0) return HS_OK;
+
+    const auto &L = db->sorted_len;
+    const int64_t long_end = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
+    DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
+    ScanTrace tr{nullptr, nullptr};
+    if (db->trace) {
+        tr.start = static_cast<cudaEvent_t>(db->trace->scan_start);
+        tr.stop = static_cast<cudaEvent_t>(db->trace->scan_stop);
+    }
+    int launches = 0;
+    e = launch_prof_offsets(bl, st);
+    launches++;
+    if (e == cudaSuccess)
+        e = launch_scan_batch(v, db->d_cumres, long_end, kp, bl, nchunk, ctas_per_sm, db->num_sms, st,
+                              db->trace ? &tr : nullptr, &launches);
+    if (e == cudaSuccess && nhits > 0) e = launch_topk_batch(bl, db->n, k, nhits, st, &launches);
+    if (e == cudaSuccess && nhits > 0)
+        e = launch_replay_batch(v, kp, bl, nhits, k, d_hits, d_ops, ops_cap, d_ops_used, d_status, st, &launches);
+    if (db->trace) db->trace->launches = launches;
+    return from_cuda(e);
+}
+
+int hs_search_batch(hs_db *db, int32_t nq, const uint8_t *queries, const int64_t *qoffsets, const uint64_t *seeds,
+                    const hs_params *p, int32_t k, const hs_batch_tuning *tuning, void *stream, hs_hit *hits_out,
+                    int32_t *n_hits_out, uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used)
+{
+    if (!db || !p || !n_hits_out || !ops_used || nq < 0) return HS_EINVAL;
+    if (nq > 0 && (!queries || !qoffsets || !seeds)) return HS_EINVAL;
+    if (k < 0 || k > HS_MAX_K || ops_cap < 0) return HS_EINVAL;
+    int rc = hs_params_check(p);
+    if (rc != HS_OK) return rc;
+    if (nq == 0) { *n_hits_out = 0; *ops_used = 0; return HS_OK; }
+    if (qoffsets[0] != 0) return HS_EINVAL;
+    int32_t max_qlen = 0;
+    for (int32_t i = 0; i < nq; i++) {
+        const int64_t ql = qoffsets[i + 1] - qoffsets[i];
+        if (ql < 1) return HS_EINVAL;
+        if (ql > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+        max_qlen = std::max<int32_t>(max_qlen, (int32_t)ql);
+    }
+    const int64_t total = qoffsets[nq];
+    for (int64_t i = 0; i < total; i++)
+        if (queries[i] >= kNSym) return HS_EINVAL;
+    const int32_t nhits = (int32_t)std::min<int64_t>(k, db->n);
+    if (nhits > 0 && !hits_out) return HS_EINVAL;
+
+    // device/host staging: [queries | qoffsets | seeds | hits | meta | ops]
+    const size_t o_q = 0, o_off = align256((size_t)total), o_seed = o_off + align256(sizeof(int64_t) * (nq + 1));
+    const size_t o_hits = o_seed + align256(sizeof(uint64_t) * nq);
+    const size_t o_meta = o_hits + align256(sizeof(hs_hit) * (size_t)nq * std::max(k, 1));
+    const int64_t cap = hs_batch_ops_capacity(nq, total, k);
+    const size_t o_ops = o_meta + 256, io_total = o_ops + align256(sizeof(uint32_t) * (size_t)std::max<int64_t>(cap, 1));
+    rc = ensure_host_state(db, batch_layout(db->n, nq, total, max_qlen, k, nullptr, nullptr), io_total);
+    if (rc != HS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *h = db->h_io, *d = db->d_io;
+    std::memcpy(h + o_q, queries, (size_t)total);
+    std::memcpy(h + o_off, qoffsets, sizeof(int64_t) * (nq + 1));
+    std::memcpy(h + o_seed, seeds, sizeof(uint64_t) * nq);
+    cudaError_t e = cudaMemcpyAsync(d, h, o_hits, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    rc = hs_search_batch_device(db, nq, reinterpret_cast<const uint8_t *>(d + o_q),
+                                reinterpret_cast<const int64_t *>(d + o_off), reinterpret_cast<const uint64_t *>(d + o_seed),
+                                total, max_qlen, p, k, tuning, stream, db->d_ws, db->ws_bytes,
+                                reinterpret_cast<hs_hit *>(d + o_hits), reinterpret_cast<uint32_t *>(d + o_ops), cap,
+                                reinterpret_cast<int64_t *>(d + o_meta), reinterpret_cast<int32_t *>(d + o_meta + 8));
+    if (rc != HS_OK) return rc;
+    // hits and status first, then only the ops actually written
+    e = cudaMemcpyAsync(h + o_hits, d + o_hits, o_ops - o_hits, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
     int64_t used;
     int32_t status;
-    std::memcpy(&used, h + l.meta, sizeof(used));
-    std::memcpy(&status, h + l.meta + 8, sizeof(status));
-    if (nhits == 0) used = 0;
+    std::memcpy(&used, h + o_meta, sizeof(used));
+    std::memcpy(&status, h + o_meta + 8, sizeof(status));
     if (status != HS_OK) return status;
-    if (nhits > 0) std::memcpy(hits_out, h + l.hits, sizeof(hs_hit) * (size_t)nhits);
+    if (nhits == 0) used = 0;
+    if (used > 0) {
+        e = cudaMemcpyAsync(h + o_ops, d + o_ops, sizeof(uint32_t) * (size_t)used, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (nhits > 0) std::memcpy(hits_out, h + o_hits, sizeof(hs_hit) * (size_t)nq * k);
     *n_hits_out = nhits;
     *ops_used = used;
     if (used > ops_cap) return HS_ETRUNC;
-    if (used > 0) std::memcpy(ops_out, h + l.ops, sizeof(uint32_t) * (size_t)used);
+    if (used > 0) std::memcpy(ops_out, h + o_ops, sizeof(uint32_t) * (size_t)used);
     return HS_OK;
 }
 
@@ -445,12 +698,14 @@ int hs_get_alignment(hs_db *db, const uint8_t *query, int32_t qlen, const hs_par
     if (!db || !query || !p || cap < 0 || (cap > 0 && !ops_out)) return HS_EINVAL;
     if (qlen < 1) return HS_EINVAL;
     if (qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
+    db_index -= db->index_base;             // hits report global indices
     if (db_index < 0 || db_index >= db->n) return HS_EINVAL;
     for (int32_t i = 0; i < qlen; i++)
         if (query[i] >= kNSym) return HS_EINVAL;
     KParams kp;
     int rc = make_kparams(p, qlen, seed, &kp);
     if (rc != HS_OK) return rc;
+    kp.s.index_base = db->index_base;
     // ops of one pair: at most 2 per step plus the tail
     const int64_t need = slot_stride_for(qlen);
     IoLayout l = io_layout(qlen, 1);

@@ -359,12 +359,12 @@ struct PairCtx {
 };
 
 template <bool EMIT>
-__device__ __forceinline__ int32_t align_round(const PairCtx &c, const KParams &kp, uint64_t d, int r,
+__device__ __forceinline__ int32_t align_round(const PairCtx &c, const SParams &kp, uint64_t d, int r,
                                                int lane, int64_t &cells, OpWriter *ow, Span *span)
 {
     const int32_t nl = c.qsmall ? c.tlen : c.qlen, ns = c.qsmall ? c.qlen : c.tlen;
     DrawStream ds;
-    ds.init(kp.seed, d, (uint64_t)r);
+    ds.init(kp.seed, d + (uint64_t)kp.index_base, (uint64_t)r);   // draws keyed by the global index
     // lf = MAX(minFactor, LFactor*random()), sf likewise (Fig. 1, Sec. III.B.1)
     uint32_t lf = (uint32_t)(((uint64_t)kp.lf_q16 * ds.get(0)) >> 16);
     uint32_t sf = (uint32_t)(((uint64_t)kp.sf_q16 * ds.get(1)) >> 16);
@@ -411,7 +411,7 @@ __device__ __forceinline__ int32_t align_round(const PairCtx &c, const KParams &
 }
 
 // AlignSequences (Fig. 1): best of `rounds` (strict '>', first best wins).
-__device__ __forceinline__ int32_t align_pair(const PairCtx &c, const KParams &kp, uint64_t d, int lane,
+__device__ __forceinline__ int32_t align_pair(const PairCtx &c, const SParams &kp, uint64_t d, int lane,
                                               int64_t &cells, int *best_round)
 {
     int32_t best = INT_MIN;

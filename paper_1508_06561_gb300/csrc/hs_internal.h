@@ -23,16 +23,23 @@ constexpr int kCodesPad = 64;           // readable bytes past the last residue
 __host__ __device__ inline int profile_stride(int qlen) { return (qlen + 16) | 1; }
 __host__ __device__ inline int64_t profile_words(int qlen) { return (int64_t)kNSym * profile_stride(qlen); }
 
-// Everything a kernel needs to score pairs; passed by value as a kernel
-// argument, so launching needs no host->device copy of the parameters.
-struct KParams {
-    int8_t m[kNSym * kNSym];            // M[query letter][target letter]
+// What the scan and replay need to score pairs of one query; passed by
+// value as kernel arguments, so launching needs no parameter copies.
+struct SParams {
     int32_t bias;                       // -min(M): M + bias >= 0
     int32_t flush;                      // byte-lane flush interval: floor(255 / (max-min))
     int32_t pgp, gop, gep, rounds;
     uint32_t lf_q16, sf_q16, minf_q16;  // LFactor, SFactor, MinFactor in Q16
     int32_t qlen;
     uint64_t seed;
+    int64_t index_base;                 // database index of the first loaded sequence (shards)
+    int32_t min_score;                  // replay only hits scoring >= this (threshold search)
+};
+
+// The matrix (for building profiles) plus the scoring parameters.
+struct KParams {
+    int8_t m[kNSym * kNSym];            // M[query letter][target letter]
+    SParams s;
 };
 
 // Device view of a loaded database.
@@ -62,6 +69,29 @@ enum Counter { kQsLong = 0, kQsShort = 1, kQlLong = 2, kQlShort = 3, kTopkTicket
 
 constexpr int kTopkCtas = 152;
 
+// Device layout of a batched search (many queries, one scan launch).
+struct BatchLayout {
+    int32_t nq, max_qlen;
+    const uint8_t *queries;             // letters of all queries
+    const int64_t *qoffsets;            // [nq + 1]
+    const uint64_t *seeds;              // [nq]
+    int64_t *prof_off;                  // [nq] word offset of each query's two profiles
+    uint32_t *prof;                     // profiles of every query
+    int64_t *bounds;                    // [nchunk + 1] chunk boundaries in the length order
+    int32_t *scores;                    // [nq][n]
+    unsigned *counters;                 // item counter, replay ticket, then one top-k ticket per query
+    unsigned *item_ctr, *replay_ticket, *topk_tickets;
+    uint64_t *cand;                     // [nq][kTopkCtas * k]
+    int64_t *hit_idx;                   // [nq * k]
+    int32_t *hit_score;                 // [nq * k]
+    uint32_t *slots;                    // [nq * k][slot_stride]
+    int64_t slot_stride;
+    int32_t *slot_len;                  // [nq * k]
+    int64_t counter_bytes;
+};
+constexpr int kMaxChunks = 8192;
+constexpr int kDefaultChunks = 1024;
+
 size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k);
 Workspace carve_workspace(void *base, int64_t n, int32_t qlen, int32_t k);
 int64_t slot_stride_for(int32_t qlen);
@@ -80,6 +110,17 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
                         cudaStream_t st, const ScanTrace *trace, int *launches);
 size_t scan_smem_bytes(int32_t qlen);
 cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches);
+cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32_t nhits, cudaStream_t st,
+                              int *launches);
+cudaError_t launch_prof_offsets(const BatchLayout &bl, cudaStream_t st);
+cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
+                              const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
+                              cudaStream_t st, const ScanTrace *trace, int *launches);
+cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const BatchLayout &bl, int32_t nhits,
+                                int32_t k, hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
+                                int32_t *d_status, cudaStream_t st, int *launches);
+cudaError_t launch_count_at_least(const int32_t *scores, int64_t n, int32_t threshold, int64_t *d_count,
+                                  int num_sms, cudaStream_t st, int *launches);
 cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParams &kp,
                           const Workspace &ws, int32_t nhits, hs_hit *d_hits, uint32_t *d_ops,
                           int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st,

@@ -1,5 +1,6 @@
 // hs_scan.cu -- the database scan (every pair's score) and the alignment
-// replay of the ranked hits.  Database-search form of Fig. 1 (Sec. III.B.3).
+// replay of the ranked hits.  Database-search form of Fig. 1 (Sec. III.B.3),
+// for one query (plain) or many (batched).
 #include <cuda_runtime.h>
 
 #include "hs_device.cuh"
@@ -9,43 +10,61 @@ namespace hs {
 // ---------------------------------------------------------------------------
 // Profile preparation: both role profiles (reversed and forward query) into
 // global memory, once per search; the scan CTAs copy theirs into shared
-// memory and the replay reads them in place.
+// memory and the replay reads them in place.  Batched: blockIdx.y = query.
 // ---------------------------------------------------------------------------
-__global__ void profile_kernel(const uint8_t *__restrict__ q, KParams kp, uint32_t *__restrict__ prof)
+struct ProfileJob {
+    const uint8_t *queries;       // letters of all queries
+    const int64_t *qoffsets;      // nullptr: one query of length qlen at queries
+    const int64_t *prof_off;      // word offset of each query's profiles (batched)
+    int32_t qlen;
+    uint32_t *prof;
+};
+
+__global__ void profile_kernel(ProfileJob job, KParams kp)
 {
     __shared__ int8_t msm[kNSym * kNSym];
     for (int i = threadIdx.x; i < kNSym * kNSym; i += blockDim.x) msm[i] = kp.m[i];
     __syncthreads();
-    const int R = profile_stride(kp.qlen);
-    const int64_t words = profile_words(kp.qlen);
+    const uint8_t *q = job.queries;
+    int qlen = job.qlen;
+    uint32_t *prof = job.prof;
+    if (job.qoffsets) {
+        const int qi = blockIdx.y;
+        q += job.qoffsets[qi];
+        qlen = (int)(job.qoffsets[qi + 1] - job.qoffsets[qi]);
+        prof += job.prof_off[qi];
+    }
+    const int R = profile_stride(qlen);
+    const int64_t words = profile_words(qlen);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * words;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const bool rev = idx < words;
         const int64_t i = rev ? idx : idx - words;
         const int a = (int)(i / R), s = (int)(i - (int64_t)a * R);
-        prof[idx] = profile_word_value(q, kp.qlen, rev, msm, kp.bias, a, s);
+        prof[idx] = profile_word_value(q, qlen, rev, msm, kp.s.bias, a, s);
     }
 }
 
 // ---------------------------------------------------------------------------
-// The scan.  A persistent grid over one queue of length-ordered database
-// positions (longest first).  Every lane of a warp owns one pair: its O(1)
-// state (Sec. III.B.4) -- positions, step, score, best round, size factors,
-// one cached Philox block -- sits in that lane's registers, so the step
-// bookkeeping of 32 pairs runs as one SIMT instruction stream.  Each round of
-// the loop plans one step for every held pair.  Small steps (at most
-// kLocalIters chunk iterations) are scored by their own lane; the others one
-// at a time by the whole warp (coop_scan), reading the step's plan from the
-// warp's shared-memory plan slots.  Targets of >= kLongLen letters are taken
-// one per warp (only lane 0 holds a pair) so each gets the warp alone.
+// The pair loop shared by the plain and batched scans.  Every lane of a warp
+// owns one pair: its O(1) state (Sec. III.B.4) -- positions, step, score,
+// best round, size factors, one cached Philox block -- sits in that lane's
+// registers, so the step bookkeeping of 32 pairs runs as one SIMT
+// instruction stream.  Each round of the loop plans one step for every held
+// pair.  Small steps (at most kLocalIters chunk iterations) are scored by
+// their own lane; the others one at a time by the whole warp (coop_scan),
+// reading the step's plan from the warp's shared-memory plan slots.
+// Positions come from a queue over the length-ordered database (longest
+// first); targets of >= kLongLen letters are taken one per warp (only lane 0
+// holds a pair) so each gets the warp alone.
 // ---------------------------------------------------------------------------
 constexpr int kLocalIters = 64;
 
-struct ScanQueue {
-    int64_t begin, long_end, end;   // sorted positions [begin, end); [begin, long_end) long
-    uint32_t *ctr;
-    int64_t smem_words;             // profile words staged into shared memory
-    int rev_off, fwd_off;           // word offsets of the two role profiles (-1: absent)
+struct QueryCtx {
+    const uint32_t *prof_rev;       // profile for pairs where the query is the small sequence
+    const uint32_t *prof_fwd;       // ... and where it is the large one
+    int32_t *scores;                // [n] by database index
+    int64_t *cells;                 // optional [n]
 };
 
 struct Lane {                       // one pair held by one lane
@@ -59,12 +78,12 @@ struct Lane {                       // one pair held by one lane
     uint64_t w0, w1, w2, w3;
 };
 
-__device__ __forceinline__ uint32_t lane_draw(Lane &L, const KParams &kp, uint64_t i)
+__device__ __forceinline__ uint32_t lane_draw(Lane &L, const SParams &sp, uint64_t i)
 {
     const int64_t b = (int64_t)(i >> 4);
     if (b != L.blk) {
         uint64_t o[4];
-        philox4x64_10((uint64_t)L.d, (uint64_t)L.round, (uint64_t)b, 0, kp.seed, 0, o);
+        philox4x64_10((uint64_t)(L.d + sp.index_base), (uint64_t)L.round, (uint64_t)b, 0, sp.seed, 0, o);
         L.w0 = o[0]; L.w1 = o[1]; L.w2 = o[2]; L.w3 = o[3];
         L.blk = b;
     }
@@ -74,57 +93,51 @@ __device__ __forceinline__ uint32_t lane_draw(Lane &L, const KParams &kp, uint64
 }
 
 // Start round L.round: lf = MAX(minFactor, LFactor*random()), sf likewise.
-__device__ __forceinline__ void lane_start_round(Lane &L, const KParams &kp)
+__device__ __forceinline__ void lane_start_round(Lane &L, const SParams &sp)
 {
     L.blk = -1;
-    uint32_t lf = (uint32_t)(((uint64_t)kp.lf_q16 * lane_draw(L, kp, 0)) >> 16);
-    uint32_t sf = (uint32_t)(((uint64_t)kp.sf_q16 * lane_draw(L, kp, 1)) >> 16);
-    L.lf = max(lf, kp.minf_q16);
-    L.sf = max(sf, kp.minf_q16);
+    uint32_t lf = (uint32_t)(((uint64_t)sp.lf_q16 * lane_draw(L, sp, 0)) >> 16);
+    uint32_t sf = (uint32_t)(((uint64_t)sp.sf_q16 * lane_draw(L, sp, 1)) >> 16);
+    L.lf = max(lf, sp.minf_q16);
+    L.sf = max(sf, sp.minf_q16);
     L.Lp = 0; L.Sp = 0; L.step = 0; L.score = 0;
 }
 
 // Finish every round whose loop has ended (Fig. 1: "append the remaining
 // with dashes"; AlignSequences keeps the first best round), then the pair.
-__device__ __forceinline__ void lane_settle(Lane &L, const KParams &kp, int32_t *scores, int64_t *cells_out)
+__device__ __forceinline__ void lane_settle(Lane &L, const SParams &sp, const QueryCtx &qc)
 {
     while (L.d >= 0 && !(L.Lp < L.nl && L.Sp < L.ns)) {
-        L.score -= kp.pgp * ((L.nl - L.Lp) + (L.ns - L.Sp));
+        L.score -= sp.pgp * ((L.nl - L.Lp) + (L.ns - L.Sp));
         if (L.score > L.best) L.best = L.score;
         L.round++;
-        if (L.round < kp.rounds) {
-            lane_start_round(L, kp);
+        if (L.round < sp.rounds) {
+            lane_start_round(L, sp);
         } else {
-            scores[L.d] = L.best;
-            if (cells_out) cells_out[L.d] = L.cells;
+            qc.scores[L.d] = L.best;
+            if (qc.cells) qc.cells[L.d] = L.cells;
             L.d = -1;
         }
     }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
-scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParams kp,
-            int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
-{
-    extern __shared__ uint4 smem_raw[];
-    __shared__ Plan plans[kWarpsPerCta][32];
-    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
-    const int S = profile_stride(kp.qlen);
-    {
-        const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
-        const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
-        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
-    }
-    __syncthreads();
+// Queue positions [begin, end) of the length order; [begin, long_end) long.
+struct PosQueue {
+    int64_t begin, long_end, end;
+    unsigned *ctr;                  // global or shared counter of handed-out positions
+};
 
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, const QueryCtx &qc,
+                                          const PosQueue &qu, Plan *plans, int lane)
+{
+    const int R = profile_stride(sp.qlen);
     const unsigned lt_mask = (1u << lane) - 1u;
     Lane L = {};
     L.d = -1;
     L.t = db.codes;
     L.best = INT_MIN;
     int phase = qu.long_end > qu.begin ? 0 : 1;       // 0: one long target per warp
-    bool open = true;
+    bool open = qu.end > qu.begin;
     for (;;) {
         // refill empty lanes from the queue
         if (open) {
@@ -133,7 +146,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
             if (need) {
                 const int m = __popc(need);
                 long long base = 0;
-                if (lane == 0) base = (long long)qu.begin + (long long)atomicAdd(qu.ctr, (uint32_t)m);
+                if (lane == 0) base = (long long)qu.begin + (long long)atomicAdd(qu.ctr, (unsigned)m);
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 if (base + m >= qu.end) open = false;
                 if (phase == 0 && base >= qu.long_end) phase = 1;
@@ -143,14 +156,14 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
                     const int64_t off = db.offsets[L.d];
                     const int32_t tlen = (int32_t)(db.offsets[L.d + 1] - off);
                     L.t = db.codes + off;
-                    L.qsmall = tlen >= kp.qlen;            // the target is large on ties
-                    L.nl = L.qsmall ? tlen : kp.qlen;
-                    L.ns = L.qsmall ? kp.qlen : tlen;
+                    L.qsmall = tlen >= sp.qlen;            // the target is large on ties
+                    L.nl = L.qsmall ? tlen : sp.qlen;
+                    L.ns = L.qsmall ? sp.qlen : tlen;
                     L.round = 0;
                     L.best = INT_MIN;
                     L.cells = 0;
-                    lane_start_round(L, kp);
-                    lane_settle(L, kp, scores, cells_out);   // empty small sequence
+                    lane_start_round(L, sp);
+                    lane_settle(L, sp, qc);                 // empty small sequence
                 }
             }
         }
@@ -165,18 +178,17 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
         if (busy) {
             const int32_t Lrem = L.nl - L.Lp, Srem = L.ns - L.Sp;
             const int32_t ls = max((int32_t)(((uint64_t)Lrem * L.lf) >> 16), 1);
-            const uint64_t u = lane_draw(L, kp, 2 + (uint64_t)L.step);
+            const uint64_t u = lane_draw(L, sp, 2 + (uint64_t)L.step);
             const int64_t ssw = (int64_t)(((uint64_t)Srem * L.sf * u) >> 32);
             g.ls = ls;
             g.ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
             const int64_t iters = (int64_t)((ls - g.ss + 4) >> 2) * (g.ss + (L.qsmall ? 3 : 0));
             local = iters <= kLocalIters;
             if (local) {
-                lane_scan(prof + (L.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, g, kp.bias, kp.flush,
-                          vmax, kstar);
+                lane_scan(L.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, g, sp.bias, sp.flush, vmax, kstar);
             } else {
                 plan_grid(g);
-                plans[threadIdx.x >> 5][lane] = g;
+                plans[lane] = g;
             }
         }
         __syncwarp();
@@ -185,23 +197,56 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, KParam
         while (coop) {
             const int i = __ffs(coop) - 1;
             coop &= coop - 1;
-            const Plan h = plans[threadIdx.x >> 5][i];
+            const Plan h = plans[i];
             int32_t v, k;
-            coop_scan(prof + (h.qsmall ? qu.rev_off : qu.fwd_off), S, kp.qlen, h, kp.bias, kp.flush, lane, v, k);
+            coop_scan(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
             if (lane == i) { vmax = v; kstar = k; }
         }
         // consume (Fig. 1: delete the used-up parts) and score incrementally (A17)
         if (busy) {
             L.cells += (int64_t)(g.ls - g.ss + 1) * g.ss;
             int32_t gap = 0;
-            if (kstar > 0) gap = (L.step == 0) ? kp.pgp * kstar : kp.gop + (kstar - 1) * kp.gep;
+            if (kstar > 0) gap = (L.step == 0) ? sp.pgp * kstar : sp.gop + (kstar - 1) * sp.gep;
             L.score += vmax - gap;
             L.Lp += kstar + g.ss;
             L.Sp += g.ss;
             L.step++;
-            lane_settle(L, kp, scores, cells_out);
+            lane_settle(L, sp, qc);
         }
+        __syncwarp();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Plain scan: a persistent grid over one queue of the whole database.
+// ---------------------------------------------------------------------------
+struct ScanQueue {
+    int64_t begin, long_end, end;
+    unsigned *ctr;
+    int64_t smem_words;             // profile words staged into shared memory
+    int rev_off, fwd_off;           // word offsets of the two role profiles
+};
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
+scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
+            int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
+{
+    extern __shared__ uint4 smem_raw[];
+    __shared__ Plan plans[kWarpsPerCta][32];
+    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    {
+        const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
+        const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
+        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+    }
+    __syncthreads();
+    QueryCtx qc;
+    qc.prof_rev = prof + qu.rev_off;
+    qc.prof_fwd = prof + qu.fwd_off;
+    qc.scores = scores;
+    qc.cells = cells_out;
+    const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
+    run_pairs(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
 size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
@@ -213,8 +258,9 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
                         cudaStream_t st, const ScanTrace *trace, int *launches)
 {
-    const int64_t words = profile_words(kp.qlen);
-    profile_kernel<<<64, 256, 0, st>>>(d_query, kp, ws.prof);
+    const int64_t words = profile_words(kp.s.qlen);
+    ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof};
+    profile_kernel<<<64, 256, 0, st>>>(job, kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int nl = 1;
@@ -222,7 +268,7 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
     ScanQueue qs[2];
     const uint32_t *srcs[2];
     int nq = 0;
-    if (fuse_roles(kp.qlen)) {
+    if (fuse_roles(kp.s.qlen)) {
         ScanQueue &q = qs[nq];
         q.begin = 0; q.end = db.n; q.long_end = min(long_end, split);
         q.ctr = ws.counters + kQsLong;
@@ -233,14 +279,14 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
             ScanQueue &q = qs[nq];
             q.begin = 0; q.end = split; q.long_end = min(long_end, split);
             q.ctr = ws.counters + kQsLong;
-            q.smem_words = words; q.rev_off = 0; q.fwd_off = -1;
+            q.smem_words = words; q.rev_off = 0; q.fwd_off = 0;
             srcs[nq++] = ws.prof;
         }
         if (split < db.n) {
             ScanQueue &q = qs[nq];
             q.begin = split; q.end = db.n; q.long_end = split;   // every target is shorter than the query
             q.ctr = ws.counters + kQlLong;
-            q.smem_words = words; q.rev_off = -1; q.fwd_off = 0;
+            q.smem_words = words; q.rev_off = 0; q.fwd_off = 0;
             srcs[nq++] = ws.prof + words;
         }
     }
@@ -256,7 +302,8 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kWarpsPerCta * 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp, ws.scores, d_cells);
+        scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores,
+                                                                        d_cells);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         nl++;
@@ -270,24 +317,159 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
 }
 
 // ---------------------------------------------------------------------------
+// Batched scan: many queries against the resident database in one
+// persistent launch.  Work items are (query, chunk) in query-major order;
+// chunks are contiguous ranges of the length order with about equal
+// residues, so the long targets of each query spread over many items.  A CTA
+// takes an item, stages the query's profile for the role of the chunk's
+// first (longest) target in shared memory -- only when the query or role
+// changes -- and its warps run the pair loop over the chunk's positions from a
+// CTA-shared counter.  Pairs of the other role (the one chunk per query that
+// straddles the role switch) read that role's profile from global memory.
+// ---------------------------------------------------------------------------
+__global__ void chunk_bounds_kernel(const int64_t *cumres, int64_t n, int32_t nchunk, int64_t *bounds)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nchunk) return;
+    const int64_t total = cumres[n];
+    const int64_t target = (int64_t)((double)total * c / nchunk);
+    int64_t lo = 0, hi = n;                 // first position whose cumulative residues reach target
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cumres[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    bounds[c] = c == nchunk ? n : lo;
+}
+
+struct BatchScan {
+    int32_t nq, nchunk;
+    const int64_t *qoffsets;        // [nq + 1]
+    const uint64_t *seeds;          // [nq]
+    const int64_t *prof_off;        // [nq] word offsets into prof
+    const uint32_t *prof;           // both role profiles of every query
+    const int64_t *bounds;          // [nchunk + 1]
+    int64_t long_end;
+    int32_t *scores;                // [nq][n]
+    unsigned *item_ctr;
+};
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 2)
+scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
+{
+    extern __shared__ uint4 smem_raw[];
+    __shared__ Plan plans[kWarpsPerCta][32];
+    __shared__ long long s_item;
+    __shared__ unsigned s_pos;
+    const uint32_t *prof_s = reinterpret_cast<const uint32_t *>(smem_raw);
+    int cur_q = -1, cur_role = -1;
+    const long long nitems = (long long)bs.nq * bs.nchunk;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = (long long)atomicAdd(bs.item_ctr, 1u);
+            s_pos = 0;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= nitems) break;
+        const int q = (int)(item / bs.nchunk), c = (int)(item - (long long)q * bs.nchunk);
+        const int64_t b0 = bs.bounds[c], b1 = bs.bounds[c + 1];
+        if (b0 < b1) {
+            SParams sp = sp0;
+            sp.qlen = (int32_t)(bs.qoffsets[q + 1] - bs.qoffsets[q]);
+            sp.seed = bs.seeds[q];
+            const int64_t d0 = db.order[b0];
+            const int role = (db.offsets[d0 + 1] - db.offsets[d0]) >= sp.qlen ? 0 : 1;
+            const int64_t words = profile_words(sp.qlen);
+            const uint32_t *pg = bs.prof + bs.prof_off[q];
+            if (q != cur_q || role != cur_role) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(pg + (role ? words : 0));
+                for (int64_t i = threadIdx.x; i < words / 4; i += blockDim.x) smem_raw[i] = src[i];
+                cur_q = q;
+                cur_role = role;
+            }
+            __syncthreads();
+            QueryCtx qc;
+            qc.prof_rev = role == 0 ? prof_s : pg;
+            qc.prof_fwd = role == 1 ? prof_s : pg + words;
+            qc.scores = bs.scores + (int64_t)q * db.n;
+            qc.cells = nullptr;
+            const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
+            run_pairs(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
+                              const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
+                              cudaStream_t st, const ScanTrace *trace, int *launches)
+{
+    ProfileJob job = {bl.queries, bl.qoffsets, bl.prof_off, 0, bl.prof};
+    profile_kernel<<<dim3(16, bl.nq), 256, 0, st>>>(job, kp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    chunk_bounds_kernel<<<(nchunk + 1 + 255) / 256, 256, 0, st>>>(d_cumres, db.n, nchunk, bl.bounds);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    BatchScan bs;
+    bs.nq = bl.nq;
+    bs.nchunk = nchunk;
+    bs.qoffsets = bl.qoffsets;
+    bs.seeds = bl.seeds;
+    bs.prof_off = bl.prof_off;
+    bs.prof = bl.prof;
+    bs.bounds = bl.bounds;
+    bs.long_end = long_end;
+    bs.scores = bl.scores;
+    bs.item_ctr = bl.item_ctr;
+    const size_t smem = (size_t)profile_words(bl.max_qlen) * 4;
+    e = cudaFuncSetAttribute(scan_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_batch_kernel, kWarpsPerCta * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
+    if (trace && trace->start) {
+        e = cudaEventRecord(trace->start, st);
+        if (e != cudaSuccess) return e;
+    }
+    scan_batch_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, bs, kp.s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (trace && trace->stop) {
+        e = cudaEventRecord(trace->stop, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (launches) *launches += 3;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
 // Replay of the ranked hits.  One warp per hit reruns the pair with the same
 // draws (so the scan itself never stores an alignment), checks the score
 // against the scan's, and writes the winning round's run-length ops into the
 // hit's slot.  The last CTA to finish packs the slots into the caller's ops
-// buffer and fills in the offsets.
+// buffer and fills in the offsets.  Batched: hit i belongs to query i / nhits.
 // ---------------------------------------------------------------------------
 struct ReplayArgs {
-    const uint32_t *prof;           // reversed profile, forward at + words
-    int64_t words;
+    const uint8_t *queries;         // letters (all queries when batched)
+    const int64_t *qoffsets;        // nullptr: one query (sp.qlen, sp.seed)
+    const uint64_t *seeds;          // batched: per query
+    const int64_t *prof_off;        // batched: per query word offset into prof
+    const uint32_t *prof;           // reversed profile, forward at + profile_words(qlen)
     const int64_t *hit_idx;         // nullptr: the single pair `single_index`
     int64_t single_index;
     const int32_t *hit_score;       // expected scores (nullptr: not checked)
-    int32_t nhits;
-    uint32_t *slots;                // nhits * slot_stride
+    int32_t nhits;                  // hits per query
+    int32_t k;                      // slot stride between queries, in hits
+    int32_t nq;
+    uint32_t *slots;                // (nq * k) * slot_stride
     int64_t slot_stride;
     int32_t *slot_len;
-    hs_hit *hits;
-    uint32_t *ticket;               // nullptr: single pair, slots are the output
+    hs_hit *hits;                   // nq * k records (query i at i * k)
+    unsigned *ticket;               // nullptr: single pair, slots are the output
     uint32_t *ops;
     int64_t ops_cap;
     int64_t *ops_used;
@@ -299,39 +481,54 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
     atomicCAS(status, (int32_t)HS_OK, code);
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, KParams kp, ReplayArgs ra)
+__global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SParams sp0, ReplayArgs ra)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * kWarpsPerCta + warp;
-    if (i < ra.nhits) {
-        const int64_t d = ra.hit_idx ? ra.hit_idx[i] : ra.single_index;
+    const int w = blockIdx.x * kWarpsPerCta + warp;     // hit number over all queries
+    const int per = max(ra.nhits, 1);
+    const int qi = w / per, i = w - qi * per;
+    if (ra.nhits > 0 && qi < ra.nq) {
+        SParams sp = sp0;
+        const uint32_t *prof = ra.prof;
+        if (ra.qoffsets) {
+            sp.qlen = (int32_t)(ra.qoffsets[qi + 1] - ra.qoffsets[qi]);
+            sp.seed = ra.seeds[qi];
+            prof += ra.prof_off[qi];
+        }
+        const int slot = qi * ra.k + i;
+        const int64_t d = ra.hit_idx ? ra.hit_idx[slot] : ra.single_index;
         const int64_t off = db.offsets[d];
         PairCtx c;
         c.t = db.codes + off;
         c.tlen = (int32_t)(db.offsets[d + 1] - off);
-        c.qlen = kp.qlen;
-        c.qsmall = c.tlen >= kp.qlen;
-        c.prof = ra.prof + (c.qsmall ? 0 : ra.words);
-        c.S = profile_stride(kp.qlen);
+        c.qlen = sp.qlen;
+        c.qsmall = c.tlen >= sp.qlen;
+        c.prof = prof + (c.qsmall ? 0 : profile_words(sp.qlen));
+        c.S = profile_stride(sp.qlen);
         int64_t cells = 0;
         int br = 0;
-        const int32_t best = align_pair(c, kp, (uint64_t)d, lane, cells, &br);
         OpWriter ow;
         Span span = {-1, -1, -1, -1};
-        ow.init(ra.slots + (int64_t)i * ra.slot_stride, ra.slot_stride);
-        const int32_t again = align_round<true>(c, kp, (uint64_t)d, br, lane, cells, &ow, &span);
+        ow.init(ra.slots + (int64_t)slot * ra.slot_stride, ra.slot_stride);
+        int32_t best, again;
+        if (ra.hit_score && ra.hit_score[slot] < sp.min_score) {
+            best = again = ra.hit_score[slot];      // below the reporting threshold: no alignment
+        } else {
+            best = align_pair(c, sp, (uint64_t)d, lane, cells, &br);
+            again = align_round<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span);
+        }
         if (lane == 0) {
-            if (again != best || (ra.hit_score && ra.hit_score[i] != best)) set_status(ra.status, HS_EINTERNAL);
+            if (again != best || (ra.hit_score && ra.hit_score[slot] != best)) set_status(ra.status, HS_EINTERNAL);
             hs_hit h;
-            h.db_index = d;
+            h.db_index = d + sp.index_base;
             h.score = best;
             h.q_begin = span.qb; h.q_end = span.qe;
             h.t_begin = span.tb; h.t_end = span.te;
             h.ops_len = (int32_t)ow.n;
             h.ops_offset = 0;
-            ra.hits[i] = h;
-            ra.slot_len[i] = (int32_t)ow.n;
+            ra.hits[slot] = h;
+            ra.slot_len[slot] = (int32_t)ow.n;
             if (!ra.ticket) {
                 *ra.ops_used = ow.n;
                 if (ow.n > ra.ops_cap) set_status(ra.status, HS_ETRUNC);
@@ -348,19 +545,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, KP
     if (!is_last) return;
     __threadfence();
 
-    // pack: offsets by an exclusive scan over the hits (one warp), then copy
+    // pack: offsets by an exclusive scan over all hits (one warp), then copy
+    const int total_hits = ra.nq * ra.nhits;
     if (warp == 0) {
         int64_t carry = 0;
-        for (int base = 0; base < ra.nhits; base += 32) {
+        for (int base = 0; base < total_hits; base += 32) {
             const int j = base + lane;
-            int64_t v = j < ra.nhits ? ((volatile int32_t *)ra.slot_len)[j] : 0;
+            const int slot = j < total_hits ? (j / ra.nhits) * ra.k + j % ra.nhits : 0;
+            const int64_t v = j < total_hits ? ((volatile int32_t *)ra.slot_len)[slot] : 0;
             int64_t incl = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                 if (lane >= o) incl += y;
             }
-            if (j < ra.nhits) ((volatile int64_t *)&ra.hits[j].ops_offset)[0] = carry + incl - v;
+            if (j < total_hits) ((volatile int64_t *)&ra.hits[slot].ops_offset)[0] = carry + incl - v;
             carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         if (lane == 0) {
@@ -369,14 +568,23 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, KP
         }
     }
     __syncthreads();
-    __threadfence_block();
-    for (int j = warp; j < ra.nhits; j += kWarpsPerCta) {
-        const int64_t o = ((volatile int64_t *)&ra.hits[j].ops_offset)[0];
-        const int32_t n = ((volatile int32_t *)ra.slot_len)[j];
+    for (int j = warp; j < total_hits; j += kWarpsPerCta) {
+        const int slot = (j / ra.nhits) * ra.k + j % ra.nhits;
+        const int64_t o = ((volatile int64_t *)&ra.hits[slot].ops_offset)[0];
+        const int32_t n = ((volatile int32_t *)ra.slot_len)[slot];
         if (o + n > ra.ops_cap) continue;
-        const uint32_t *src = ra.slots + (int64_t)j * ra.slot_stride;
+        const uint32_t *src = ra.slots + (int64_t)slot * ra.slot_stride;
         for (int x = lane; x < n; x += 32) ra.ops[o + x] = ((volatile const uint32_t *)src)[x];
     }
+}
+
+static ReplayArgs replay_args_single(const uint8_t *d_query, const uint32_t *prof)
+{
+    ReplayArgs ra = {};
+    ra.queries = d_query;
+    ra.prof = prof;
+    ra.nq = 1;
+    return ra;
 }
 
 cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParams &kp,
@@ -384,15 +592,12 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
                           int64_t ops_cap, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st,
                           int *launches)
 {
-    (void)d_query;
     if (nhits <= 0) return cudaSuccess;
-    ReplayArgs ra;
-    ra.prof = ws.prof;
-    ra.words = profile_words(kp.qlen);
+    ReplayArgs ra = replay_args_single(d_query, ws.prof);
     ra.hit_idx = ws.hit_idx;
-    ra.single_index = 0;
     ra.hit_score = ws.hit_score;
     ra.nhits = nhits;
+    ra.k = nhits;
     ra.slots = ws.slots;
     ra.slot_stride = ws.slot_stride;
     ra.slot_len = ws.slot_len;
@@ -403,27 +608,56 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
     ra.ops_used = d_ops_used;
     ra.status = d_status;
     const int grid = (nhits + kWarpsPerCta - 1) / kWarpsPerCta;
-    replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp, ra);
+    replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const BatchLayout &bl, int32_t nhits,
+                                int32_t k, hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
+                                int32_t *d_status, cudaStream_t st, int *launches)
+{
+    if (nhits <= 0 || bl.nq <= 0) return cudaSuccess;
+    ReplayArgs ra = replay_args_single(bl.queries, bl.prof);
+    ra.qoffsets = bl.qoffsets;
+    ra.seeds = bl.seeds;
+    ra.prof_off = bl.prof_off;
+    ra.hit_idx = bl.hit_idx;
+    ra.hit_score = bl.hit_score;
+    ra.nhits = nhits;
+    ra.k = k;
+    ra.nq = bl.nq;
+    ra.slots = bl.slots;
+    ra.slot_stride = bl.slot_stride;
+    ra.slot_len = bl.slot_len;
+    ra.hits = d_hits;
+    ra.ticket = bl.replay_ticket;
+    ra.ops = d_ops;
+    ra.ops_cap = ops_cap;
+    ra.ops_used = d_ops_used;
+    ra.status = d_status;
+    const int64_t total = (int64_t)bl.nq * nhits;
+    const int grid = (int)((total + kWarpsPerCta - 1) / kWarpsPerCta);
+    replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
 // hs_get_alignment: the profile kernel, then one warp writing straight into
-// the caller's ops buffer.  `ws` supplies the profile and one hit slot.
+// the caller's ops buffer.  `ws` supplies the profile.
 cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KParams &kp,
                               const Workspace &ws, int64_t db_index, uint32_t *d_ops, int64_t cap,
                               hs_hit *d_hit, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st)
 {
-    profile_kernel<<<64, 256, 0, st>>>(d_query, kp, ws.prof);
+    ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof};
+    profile_kernel<<<64, 256, 0, st>>>(job, kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ReplayArgs ra;
-    ra.prof = ws.prof;
-    ra.words = profile_words(kp.qlen);
+    ReplayArgs ra = replay_args_single(d_query, ws.prof);
     ra.hit_idx = nullptr;
     ra.single_index = db_index;
-    ra.hit_score = nullptr;
     ra.nhits = 1;
+    ra.k = 1;
     ra.slots = d_ops;
     ra.slot_stride = cap;
     ra.slot_len = ws.slot_len;
@@ -433,7 +667,7 @@ cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KP
     ra.ops_cap = cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    replay_kernel<<<1, kWarpsPerCta * 32, 0, st>>>(db, kp, ra);
+    replay_kernel<<<1, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     return cudaGetLastError();
 }
 

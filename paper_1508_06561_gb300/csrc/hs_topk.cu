@@ -108,13 +108,20 @@ __device__ void gather_at_least(const Keys &key, int64_t m, uint64_t kth, uint64
     __syncthreads();
 }
 
+// Batched: blockIdx.y is the query; its scores, candidates, hits and ticket
+// sit at y * n, y * (gridDim.x * k), y * hit_stride and y.
 __global__ void __launch_bounds__(kTopkThreads)
 topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t *hit_idx,
-            int32_t *hit_score, uint32_t *ticket)
+            int32_t *hit_score, uint32_t *ticket, int32_t hit_stride)
 {
     __shared__ SelectSmem sm;
     __shared__ uint64_t sortbuf[kSortMax];
     __shared__ int is_last;
+    scores += (int64_t)blockIdx.y * n;
+    cand += (int64_t)blockIdx.y * gridDim.x * k;
+    hit_idx += (int64_t)blockIdx.y * hit_stride;
+    hit_score += (int64_t)blockIdx.y * hit_stride;
+    ticket += blockIdx.y;
 
     // phase 1: this CTA's slice
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -170,12 +177,69 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
 
 }  // namespace
 
+// Number of pairs scoring at least `threshold` (Sec. IV's threshold score).
+__global__ void count_at_least_kernel(const int32_t *scores, int64_t n, int32_t threshold,
+                                      unsigned long long *count)
+{
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += scores[i] >= threshold;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+cudaError_t launch_count_at_least(const int32_t *scores, int64_t n, int32_t threshold, int64_t *d_count,
+                                  int num_sms, cudaStream_t st, int *launches)
+{
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    count_at_least_kernel<<<num_sms * 4, 256, 0, st>>>(scores, n, threshold,
+                                                       reinterpret_cast<unsigned long long *>(d_count));
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches)
 {
     if (n <= 0 || k <= 0) return cudaSuccess;
     topk_kernel<<<ws.topk_ctas, kTopkThreads, 0, st>>>(ws.scores, n, k, ws.cand, ws.hit_idx, ws.hit_score,
-                                                       ws.counters + kTopkTicket);
+                                                       ws.counters + kTopkTicket, k);
     if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// nhits = min(k, n) best of every query; hit lists are k apart.
+cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32_t nhits, cudaStream_t st,
+                              int *launches)
+{
+    if (n <= 0 || nhits <= 0 || bl.nq <= 0) return cudaSuccess;
+    topk_kernel<<<dim3(kTopkCtas, bl.nq), kTopkThreads, 0, st>>>(bl.scores, n, nhits, bl.cand, bl.hit_idx,
+                                                                 bl.hit_score, bl.topk_tickets, k);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// Word offsets of every query's two profiles (prefix sums, one warp).
+__global__ void prof_offsets_kernel(const int64_t *qoffsets, int32_t nq, int64_t *prof_off)
+{
+    const int lane = threadIdx.x;
+    int64_t carry = 0;
+    for (int base = 0; base < nq; base += 32) {
+        const int q = base + lane;
+        const int64_t v = q < nq ? 2 * profile_words((int)(qoffsets[q + 1] - qoffsets[q])) : 0;
+        int64_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (q < nq) prof_off[q] = carry + incl - v;
+        carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+}
+
+cudaError_t launch_prof_offsets(const BatchLayout &bl, cudaStream_t st)
+{
+    prof_offsets_kernel<<<1, 32, 0, st>>>(bl.qoffsets, bl.nq, bl.prof_off);
     return cudaGetLastError();
 }
 
