@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-budget-s", type=float, default=12.0,
                     help="wall-time budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     return ap.parse_args()
 
 
@@ -212,6 +213,59 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------------
+# batched vs plain on the same queries (64 queries, lengths uniform in
+# [30, 1000], top-100: the shape of the batched workload)
+# --------------------------------------------------------------------------
+def batched_section(P, D, db, params, seed, reps=3):
+    import torch
+
+    from paper_1508_06561_gb300 import autotune, synth
+    rng = np.random.default_rng(3)
+    qs = [synth.residues(rng, int(L)) for L in rng.integers(30, 1001, 64)]
+    k = 100
+    best, tune_s = autotune.tune(D, qs, k, params)
+    cat = torch.from_numpy(np.concatenate(qs)).cuda()
+    off = np.zeros(len(qs) + 1, np.int64)
+    np.cumsum([len(q) for q in qs], out=off[1:])
+    offd = torch.from_numpy(off).cuda()
+    seeds = torch.full((len(qs),), seed, dtype=torch.int64, device="cuda")
+    mq = int(max(len(q) for q in qs))
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        out = P.search_batch_device(D, cat, offd, seeds, mq, k, params, best, st)     # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            P.search_batch_device(D, cat, offd, seeds, mq, k, params, best, st, out["workspace"], out)
+        b.record(st)
+    st.synchronize()
+    assert int(out["status"].item()) == 0
+    t_batch = a.elapsed_time(b) / 1000.0 / reps
+    # the same queries, one plain device search each
+    qd = [torch.from_numpy(q).cuda() for q in qs]
+    longest = int(np.argmax([len(q) for q in qs]))
+    with torch.cuda.stream(st):
+        o1 = P.search_device(D, qd[longest], k, params, seed=seed, stream=st)
+        ws = o1["workspace"]
+        for q in qd:
+            P.search_device(D, q, k, params, seed=seed, stream=st, workspace=ws, out=o1)
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(st)
+        for _ in range(reps):
+            for q in qd:
+                P.search_device(D, q, k, params, seed=seed, stream=st, workspace=ws, out=o1)
+        b2.record(st)
+    st.synchronize()
+    t_plain = a2.elapsed_time(b2) / 1000.0 / reps
+    res = db.residues * len(qs)
+    return {"workload": "batched-64q-u30-1000-swissprot-like-570k", "queries": len(qs), "k": k,
+            "value": res / t_batch, "unit": UNIT, "ms_per_batch": t_batch * 1000.0,
+            "plain_same_queries": res / t_plain, "plain_ms": t_plain * 1000.0,
+            "speedup_vs_plain": t_plain / t_batch, "tuning": best,
+            "tuning_candidates_ms": {kk: v * 1000.0 for kk, v in tune_s.items()}}
+
+
+# --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
@@ -334,6 +388,9 @@ def run_ours(args, world, rank, local):
     peak = sms * 128 * 4 * 2070e6 / 1e12     # INT32 lanes x 4 byte lanes x max SM clock
     traffic = recorded_traffic(cfg["workload"])
 
+    batched = None
+    if world == 1 and not args.no_batched and args.workload == "plain-large":
+        batched = batched_section(P, D, db, params, args.seed)
     cpu_rate, cpu_threads, ns, nres, tcpu = oracle_rate(db, q, args.seed, args.cpu_budget_s) \
         if world == 1 else (None, None, 0, 0, 0.0)
     line = {
@@ -349,6 +406,8 @@ def run_ours(args, world, rank, local):
                      "peak_basis": "%d SMs x 128 INT32 lanes x 4 byte-lane cells x 2070 MHz (derived)" % sms},
         "clocks": clk,
     }
+    if batched is not None:
+        line["batched"] = batched
     if cpu_rate is not None:
         line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                                 "sample": "%d random sequences (%d residues) of the same database, scores only, "
