@@ -76,6 +76,8 @@ def lib():
         L.or_score_rows.restype = C.c_int
         L.or_best_shift.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, i64p]
         L.or_best_shift.restype = C.c_int64
+        L.or_best_shift_full.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, i64p]
+        L.or_best_shift_full.restype = C.c_int64
         L.or_align_pair.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, P(Params), C.c_uint64,
                                     C.c_uint64, u8p, u8p, i64p, i32p, i64p]
         L.or_align_pair.restype = C.c_int64
@@ -153,6 +155,16 @@ def best_shift(large, small, M):
     k = C.c_int64()
     v = lib().or_best_shift(_p(large, C.c_uint8), len(large), _p(small, C.c_uint8), len(small),
                             _p(M, C.c_int8), C.byref(k))
+    return int(k.value), int(v)
+
+
+def best_shift_full(large, small, M):
+    """One full-slide getBestSubsequenceAlignment (shifts -(|small|-1) ..
+    |large|-1, overlap only): returns (k*, V(k*))."""
+    large, small, M = _u8(large), _u8(small), _mat(M)
+    k = C.c_int64()
+    v = lib().or_best_shift_full(_p(large, C.c_uint8), len(large), _p(small, C.c_uint8), len(small),
+                                 _p(M, C.c_int8), C.byref(k))
     return int(k.value), int(v)
 
 

@@ -31,6 +31,16 @@
  *   A10 ties: lowest shift, first round.
  *   A12 random(): Philox4x64-10 draws, 16 bits each (see draw16 below).
  *   A13 large = target when |T| >= |Q|.
+ * Full-slide mode (the pair-wise form of Fig. 1, without Sec. III.B.3 b):
+ *   F1  shifts k = -(ss-1) .. ls-1 (overlap >= 1), V(k) over the overlap only,
+ *       lowest k on ties;
+ *   F2  1 <= ss <= Srem (no ls bound: a piece may overhang the window);
+ *   F3  a step lays out: the letters of whichever piece starts first against
+ *       gaps in the other row, the overlap, then small's letters past the
+ *       window's end against gaps in large's row; large gives up its letters
+ *       through the end of the overlap, small its ss letters;
+ *   F4  SCORE is taken over the finished rows (so gap runs may merge across
+ *       steps, and leading/trailing runs in either row are periphery).
  * Scores use the matrix as M[query letter][target letter]; the matrix must
  * be symmetric for the library, but the oracle keeps the orientation explicit.
  *
@@ -256,6 +266,14 @@ static int64_t best_subsequence(const uint8_t *large, int64_t nl, const uint8_t 
     return best;
 }
 
+/* One full-slide step (F1), for the same check with partial overlaps. */
+int64_t or_best_shift_full(const uint8_t *large, int64_t nl, const uint8_t *small, int64_t ns,
+                           const int8_t *M, int64_t *best_k)
+{
+    int64_t cells = 0;
+    return best_subsequence(large, nl, small, ns, OR_MODE_FULL, M, 1, best_k, &cells);
+}
+
 /* Exported single-step scan, so tests can check it against an
  * independent numpy sliding-window computation. */
 int64_t or_best_shift(const uint8_t *large, int64_t nl, const uint8_t *small, int64_t ns,
@@ -283,11 +301,24 @@ static int64_t align_round(const uint8_t *large, int64_t nl, const uint8_t *smal
         if (ls < 1) ls = 1;
         uint64_t u = draw16(seed, d, r, 2 + (uint64_t)t);
         int64_t ss = (int64_t)(((uint64_t)Srem * sf * u) >> 32);
-        int64_t cap = Srem < ls ? Srem : ls;    /* A6/A7: small's piece fits in large's */
+        int64_t cap = p->mode == OR_MODE_DB ? (Srem < ls ? Srem : ls) : Srem;   /* A6/A7; F2 */
         if (ss > cap) ss = cap;
         if (ss < 1) ss = 1;
         int64_t kstar;
         best_subsequence(large + Lp, ls, small + Sp, ss, p->mode, M, q_is_large, &kstar, cells);
+        if (p->mode != OR_MODE_DB) {
+            /* F3: the step's columns for any shift, overhangs included */
+            const int64_t j0 = kstar < 0 ? -kstar : 0;                /* first overlapping small letter */
+            const int64_t j1 = (ls - kstar < ss) ? ls - kstar : ss;   /* one past the last */
+            for (int64_t j = 0; j < j0; j++) { rl[nc] = OR_GAP; rs[nc] = small[Sp + j]; nc++; }
+            for (int64_t i = 0; i < kstar; i++) { rl[nc] = large[Lp + i]; rs[nc] = OR_GAP; nc++; }
+            for (int64_t j = j0; j < j1; j++) { rl[nc] = large[Lp + kstar + j]; rs[nc] = small[Sp + j]; nc++; }
+            for (int64_t j = j1; j < ss; j++) { rl[nc] = OR_GAP; rs[nc] = small[Sp + j]; nc++; }
+            Lp += kstar + j1;
+            Sp += ss;
+            t++;
+            continue;
+        }
         /* A9: large gives up its first k*+ss letters; the first k* stand
          * against gaps in small's row, the next ss against small's piece. */
         for (int64_t i = 0; i < kstar; i++) { rl[nc] = large[Lp + i]; rs[nc] = OR_GAP; nc++; }

@@ -1,0 +1,68 @@
+"""Continuous-batching server on the GPU: requests submitted while others
+run are batched together, and every result equals a search of that query
+alone (same seed); the memory gate keeps each batch within its budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import paper_1508_06561_gb300 as P
+from paper_1508_06561_gb300 import serve, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def db():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_06561_gb300 import build
+    build.build()
+    rng = np.random.default_rng(8)
+    d = synth.db_from_lengths(rng, synth.lognormal_lengths(rng, 20000, 300, 0.6, 1, 6000))
+    D = P.Database(d.codes, d.offsets)
+    yield D
+    D.close()
+
+
+def test_results_alone_equal_results_in_the_mix(db):
+    rng = np.random.default_rng(1)
+    qs = [synth.residues(rng, int(L)) for L in synth.lognormal_lengths(rng, 80, 250, 0.6, 20, 2000)]
+    seeds = rng.integers(0, 2**62, len(qs))
+    params = P.Params()
+    srv = serve.Server(db, k=20, params=params, max_batch=16, slots=2, max_total_qlen=8192)
+    futs = []
+
+    def client(lo, hi):
+        for i in range(lo, hi):
+            futs.append((i, srv.submit(qs[i], int(seeds[i]))))
+            time.sleep(float(rng.exponential(0.0005)))
+
+    ts = [threading.Thread(target=client, args=(j * 20, (j + 1) * 20)) for j in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    res = {i: f.result(timeout=120) for i, f in futs}
+    srv.close()
+    assert max(nq for nq, _ in srv.batches) > 1            # requests were served together
+    assert sum(nq for nq, _ in srv.batches) == len(qs)
+    for i, (h, o) in res.items():
+        h0, o0 = P.search(db, qs[i], 20, params, int(seeds[i]))
+        assert np.array_equal(h, h0) and np.array_equal(o, o0)
+    assert len(srv.latencies) == len(qs)
+
+
+def test_memory_gate_bounds_every_batch(db):
+    rng = np.random.default_rng(2)
+    qs = [synth.residues(rng, int(L)) for L in rng.integers(100, 400, 30)]
+    srv = serve.Server(db, k=5, max_batch=64, slots=1, max_qlen=400, max_total_qlen=900)
+    futs = [srv.submit(q, 7) for q in qs]
+    out = [f.result(timeout=120) for f in futs]
+    srv.close()
+    assert all(total <= 900 for _, total in srv.batches)
+    assert len(out) == 30
+    h0, o0 = P.search(db, qs[-1], 5, seed=7)
+    assert np.array_equal(out[-1][0], h0) and np.array_equal(out[-1][1], o0)
