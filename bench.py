@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0,
                     help="wall-time budget of the oracle CPU baseline sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per serving rate (max)")
     return ap.parse_args()
 
 
@@ -266,6 +268,43 @@ def batched_section(P, D, db, params, seed, reps=3):
 
 
 # --------------------------------------------------------------------------
+# serving: Poisson arrivals of single-query requests (lengths lognormal,
+# median 250, clamped to [20, 2000], one seed each) against the resident
+# database, continuous batching; p50/p99 latency beside throughput
+# --------------------------------------------------------------------------
+def serving_section(P, D, db, params, max_requests, rates=(50.0, 200.0, 1000.0)):
+    from paper_1508_06561_gb300 import serve, synth
+    out = {"workload": "serving-swissprot-like-570k", "k": 100, "rates": []}
+    for rate in rates:
+        n = int(min(max_requests, max(50, rate * 4)))
+        t_arr, qs, seeds = synth.serving_stream(5, n, rate)
+        srv = serve.Server(D, k=100, params=params, max_batch=64, slots=3, max_total_qlen=65536)
+        futs = []
+        t0 = time.perf_counter()
+        for ta, q, sd in zip(t_arr, qs, seeds):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(q, int(sd)))
+        res = [f.result(timeout=600) for f in futs]
+        t_end = time.perf_counter()
+        srv.close()
+        # the same request alone must give the same answer as in the mix
+        same = True
+        for i in np.linspace(0, n - 1, 5).astype(int):
+            h0, o0 = P.search(D, qs[i], 100, params, int(seeds[i]))
+            same &= bool(np.array_equal(res[i][0], h0) and np.array_equal(res[i][1], o0))
+        lat = serve.latency_stats(srv.latencies)
+        nb = [b for b, _ in srv.batches]
+        out["rates"].append({"offered_req_s": rate, "requests": n, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+                             "mean_ms": lat["mean_ms"], "served_req_s": n / (t_end - t0),
+                             "residues_per_s": n * db.residues / (t_end - t0), "batches": len(nb),
+                             "mean_batch": float(np.mean(nb)), "max_batch": int(np.max(nb)),
+                             "alone_equals_mix": same})
+    return out
+
+
+# --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
@@ -388,9 +427,11 @@ def run_ours(args, world, rank, local):
     peak = sms * 128 * 4 * 2070e6 / 1e12     # INT32 lanes x 4 byte lanes x max SM clock
     traffic = recorded_traffic(cfg["workload"])
 
-    batched = None
+    batched = serving = None
     if world == 1 and not args.no_batched and args.workload == "plain-large":
         batched = batched_section(P, D, db, params, args.seed)
+    if world == 1 and not args.no_serving and args.workload == "plain-large":
+        serving = serving_section(P, D, db, params, args.serve_requests)
     cpu_rate, cpu_threads, ns, nres, tcpu = oracle_rate(db, q, args.seed, args.cpu_budget_s) \
         if world == 1 else (None, None, 0, 0, 0.0)
     line = {
@@ -408,6 +449,8 @@ def run_ours(args, world, rank, local):
     }
     if batched is not None:
         line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if cpu_rate is not None:
         line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                                 "sample": "%d random sequences (%d residues) of the same database, scores only, "

@@ -48,6 +48,9 @@ extern "C" {
 #define HS_MAX_K        4096
 
 #define HS_MODE_DB   0   /* Sec. III.B.3 b: small slides inside large only     */
+#define HS_MODE_FULL 1   /* Fig. 1 as printed: small slides across large with
+                            any overlap >= 1; pieces may overhang (pair-wise
+                            alignment form; not for the batched search)       */
 
 /* alignment run-length ops: op = v & 3, run length = v >> 2 */
 #define HS_OP_M 0u       /* query letter against target letter                 */
@@ -60,7 +63,7 @@ extern "C" {
  * rounds        : AlignSequences' Rounds (>= 1; 1 in database search).
  * lfactor_q16, sfactor_q16, minfactor_q16 : LFactor, SFactor, MinFactor in
  *                 Q16 fixed point (65536 == 1.0), each in [0, 65536].
- * mode          : HS_MODE_DB.
+ * mode          : HS_MODE_DB or HS_MODE_FULL.
  * matrix        : host pointer to a 24x24 row-major int8 table, entry
  *                 [a][b] scoring query letter a against target letter b;
  *                 must be symmetric.  NULL selects the built-in BLOSUM62.  */

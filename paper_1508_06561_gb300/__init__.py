@@ -34,7 +34,8 @@ class Params:
     """Sec. III.B.1 parameters; defaults are Sec. IV's (PGP=0, GOP=10, GEP=5,
     LFactor=0.5, SFactor=1, MinFactor=0.5) with Rounds=1 (Sec. III.B.3 a).
     Factors are Q16 fixed point (65536 == 1.0).  matrix: symmetric 24x24
-    int8 (query letter, target letter); None = built-in BLOSUM62."""
+    int8 (query letter, target letter); None = built-in BLOSUM62.  mode 1 is
+    the pair-wise full-slide form of Fig. 1 (HS_MODE_FULL)."""
     pgp: int = 0
     gop: int = 10
     gep: int = 5
@@ -43,10 +44,11 @@ class Params:
     sfactor_q16: int = 65536
     minfactor_q16: int = 32768
     matrix: Optional[np.ndarray] = None
+    mode: int = 0                       # 0: database search (Sec. III.B.3), 1: full slide (Fig. 1)
 
     def to_c(self):
         p = _lib.hs_params(self.pgp, self.gop, self.gep, self.rounds, self.lfactor_q16,
-                           self.sfactor_q16, self.minfactor_q16, _lib.HS_MODE_DB, None)
+                           self.sfactor_q16, self.minfactor_q16, self.mode, None)
         keep = None
         if self.matrix is not None:
             keep = np.ascontiguousarray(self.matrix, dtype=np.int8)

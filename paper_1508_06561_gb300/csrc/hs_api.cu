@@ -111,6 +111,7 @@ static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams
     sp.seed = seed;
     sp.index_base = 0;
     sp.min_score = INT_MIN;
+    sp.mode = p->mode;
     return HS_OK;
 }
 
@@ -176,7 +177,7 @@ int hs_params_check(const hs_params *p)
     if (p->pgp > HS_MAX_PENALTY || p->gop > HS_MAX_PENALTY || p->gep > HS_MAX_PENALTY) return HS_EINVAL;
     if (p->rounds < 1 || p->rounds > 1000) return HS_EINVAL;
     if (p->lfactor_q16 > 65536 || p->sfactor_q16 > 65536 || p->minfactor_q16 > 65536) return HS_EINVAL;
-    if (p->mode != HS_MODE_DB) return HS_EINVAL;
+    if (p->mode != HS_MODE_DB && p->mode != HS_MODE_FULL) return HS_EINVAL;
     if (p->matrix) {
         for (int a = 0; a < kNSym; a++)
             for (int b = 0; b < a; b++)
@@ -590,6 +591,7 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     KParams kp;
     int rc = make_kparams(p, max_qlen, 0, &kp);
     if (rc != HS_OK) return rc;
+    if (p->mode != HS_MODE_DB) return HS_EINVAL;    // the batched scan is the database-search form
     kp.s.index_base = db->index_base;
     bl.queries = d_queries;
     bl.qoffsets = d_qoffsets;

@@ -410,6 +410,132 @@ __device__ __forceinline__ int32_t align_round(const PairCtx &c, const SParams &
     return score;
 }
 
+// ---------------------------------------------------------------------------
+// Full-slide mode (Fig. 1 as printed; readings F1-F4).  getBestSubsequence-
+// Alignment slides small from overlapping large's first letter with its last
+// letter to overlapping large's last letter with its first: shifts
+// k = -(ss-1) .. ls-1, V(k) summed over the overlap only, lowest k on ties.
+// Lanes take shifts in turn and sum their overlaps cell by cell (byte 0 of a
+// profile word is the cell of its own column).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void full_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias, int lane,
+                                          int32_t &vmax, int32_t &kstar)
+{
+    const int nshift = g.ls + g.ss - 1;
+    int32_t bv = INT_MIN, bk = INT_MAX;
+    for (int x = lane; x < nshift; x += 32) {
+        const int k = x - (g.ss - 1);
+        const int j0 = max(0, -k), j1 = min(g.ss, g.ls - k);
+        int32_t v = 0;
+        if (g.qsmall) {                 // letter from the target window, reversed query column
+            const uint8_t *tl = g.t + g.Lp + k;
+            const uint32_t *pw = prof + (qlen + 3 - g.Sp);
+            for (int j = j0; j < j1; j++) v += (int32_t)(pw[tl[j] * R - j] & 0xFFu);
+        } else {                        // letter from the target piece, query column
+            const uint8_t *ts = g.t + g.Sp;
+            const uint32_t *pw = prof + (g.Lp + k + 4);
+            for (int j = j0; j < j1; j++) v += (int32_t)(pw[ts[j] * R + j] & 0xFFu);
+        }
+        v -= bias * (j1 - j0);
+        if (v > bv) { bv = v; bk = x; }   // x ascends within a lane: keeps the lowest
+    }
+    warp_argmax(bv, bk, vmax, kstar);
+    kstar -= g.ss - 1;
+}
+
+// SCORE (reading A2) kept incrementally over the runs of a growing
+// alignment, in O(1) space.  The gap runs since the last letter pair all
+// share one fate: at the next letter pair they are interior (each maximal
+// run of one row costs GOP+(n-1)GEP, so together runs*GOP + (gaps-runs)*GEP)
+// or, if no letter pair came before them, leading periphery (PGP per gap); if
+// none follows, trailing periphery (PGP per gap).  A gap run in the same row
+// as the one before it extends that run.
+struct RunScore {
+    int32_t score, matched, last_row, runs, gaps;
+    __device__ __forceinline__ void init() { score = 0; matched = 0; last_row = -1; runs = 0; gaps = 0; }
+    __device__ __forceinline__ void gap(int row, int32_t n)
+    {
+        if (n <= 0) return;
+        if (row != last_row) { runs++; last_row = row; }
+        gaps += n;
+    }
+    __device__ __forceinline__ void match(int32_t sum, const SParams &sp)
+    {
+        if (!matched) score -= sp.pgp * gaps;
+        else score -= runs * sp.gop + (gaps - runs) * sp.gep;
+        score += sum;
+        matched = 1;
+        last_row = -1; runs = 0; gaps = 0;
+    }
+    __device__ __forceinline__ void finish(const SParams &sp)
+    {
+        score -= sp.pgp * gaps;
+        last_row = -1; runs = 0; gaps = 0;
+    }
+};
+
+template <bool EMIT>
+__device__ __forceinline__ int32_t align_round_full(const PairCtx &c, const SParams &kp, uint64_t d, int r,
+                                                    int lane, int64_t &cells, OpWriter *ow, Span *span)
+{
+    const int32_t nl = c.qsmall ? c.tlen : c.qlen, ns = c.qsmall ? c.qlen : c.tlen;
+    DrawStream ds;
+    ds.init(kp.seed, d + (uint64_t)kp.index_base, (uint64_t)r);
+    uint32_t lf = (uint32_t)(((uint64_t)kp.lf_q16 * ds.get(0)) >> 16);
+    uint32_t sf = (uint32_t)(((uint64_t)kp.sf_q16 * ds.get(1)) >> 16);
+    lf = max(lf, kp.minf_q16);
+    sf = max(sf, kp.minf_q16);
+    int32_t Lp = 0, Sp = 0;
+    int64_t t = 0;
+    RunScore rs;
+    rs.init();
+    // ops: gaps in large's row hold small's letters, and vice versa
+    const uint32_t op_gl = c.qsmall ? HS_OP_I : HS_OP_D;
+    const uint32_t op_gs = c.qsmall ? HS_OP_D : HS_OP_I;
+    while (Lp < nl && Sp < ns) {
+        const int32_t Lrem = nl - Lp, Srem = ns - Sp;
+        int32_t ls = (int32_t)(((uint64_t)Lrem * lf) >> 16);
+        ls = max(ls, 1);
+        const uint64_t u = ds.get(2 + (uint64_t)t);
+        const int64_t ssw = (int64_t)(((uint64_t)Srem * sf * u) >> 32);
+        const int32_t ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)Srem));           // F2
+        Plan g = {c.t, Lp, Sp, ls, ss, c.qsmall ? 1 : 0, 0, 0, 0};
+        int32_t vmax, kstar;
+        full_scan(c.prof, c.S, c.qlen, g, kp.bias, lane, vmax, kstar);
+        cells += (int64_t)ls * ss;           // every (window letter, piece letter) pair overlaps once
+        // F3: leading overhang, overlap, trailing overhang of small
+        const int32_t j0 = max(0, -kstar), j1 = min(ss, ls - kstar);
+        rs.gap(0, j0);
+        rs.gap(1, max(kstar, 0));
+        rs.match(vmax, kp);
+        rs.gap(0, ss - j1);
+        if (EMIT && lane == 0) {
+            ow->push(op_gl, j0);
+            ow->push(op_gs, max(kstar, 0));
+            ow->push(HS_OP_M, j1 - j0);
+            ow->push(op_gl, ss - j1);
+            const int32_t lb = Lp + kstar + j0, sb = Sp + j0;
+            const int32_t qb = c.qsmall ? sb : lb, tb = c.qsmall ? lb : sb;
+            if (span->qb < 0) { span->qb = qb; span->tb = tb; }
+            span->qe = qb + (j1 - j0);
+            span->te = tb + (j1 - j0);
+        }
+        Lp += kstar + j1;
+        Sp += ss;
+        t++;
+    }
+    // "append the remaining with dashes": large's rest against gaps in small's row, or small's rest
+    rs.gap(1, nl - Lp);
+    rs.gap(0, ns - Sp);
+    rs.finish(kp);
+    if (EMIT && lane == 0) {
+        ow->push(op_gs, nl - Lp);
+        ow->push(op_gl, ns - Sp);
+        ow->flush();
+    }
+    return rs.score;
+}
+
 // AlignSequences (Fig. 1): best of `rounds` (strict '>', first best wins).
 __device__ __forceinline__ int32_t align_pair(const PairCtx &c, const SParams &kp, uint64_t d, int lane,
                                               int64_t &cells, int *best_round)
@@ -417,7 +543,8 @@ __device__ __forceinline__ int32_t align_pair(const PairCtx &c, const SParams &k
     int32_t best = INT_MIN;
     int br = 0;
     for (int r = 0; r < kp.rounds; r++) {
-        const int32_t s = align_round<false>(c, kp, d, r, lane, cells, nullptr, nullptr);
+        const int32_t s = kp.mode == HS_MODE_FULL ? align_round_full<false>(c, kp, d, r, lane, cells, nullptr, nullptr)
+                                                  : align_round<false>(c, kp, d, r, lane, cells, nullptr, nullptr);
         if (s > best) { best = s; br = r; }
     }
     if (best_round) *best_round = br;

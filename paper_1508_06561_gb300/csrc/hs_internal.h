@@ -34,6 +34,7 @@ struct SParams {
     uint64_t seed;
     int64_t index_base;                 // database index of the first loaded sequence (shards)
     int32_t min_score;                  // replay only hits scoring >= this (threshold search)
+    int32_t mode;                       // HS_MODE_DB or HS_MODE_FULL
 };
 
 // The matrix (for building profiles) plus the scoring parameters.

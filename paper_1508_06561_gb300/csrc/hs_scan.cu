@@ -249,6 +249,44 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
     run_pairs(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
+// Full-slide mode (pair-wise form): one warp per pair, pairs taken one at a
+// time from the same longest-first queue; the pair's state is warp-uniform.
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
+                 int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
+{
+    extern __shared__ uint4 smem_raw[];
+    {
+        const int64_t n16 = qu.smem_words / 4;
+        const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
+        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+    }
+    __syncthreads();
+    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        long long pos = 0;
+        if (lane == 0) pos = (long long)qu.begin + (long long)atomicAdd(qu.ctr, 1u);
+        pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+        if (pos >= qu.end) break;
+        const int64_t d = db.order[pos];
+        const int64_t off = db.offsets[d];
+        PairCtx c;
+        c.t = db.codes + off;
+        c.tlen = (int32_t)(db.offsets[d + 1] - off);
+        c.qlen = sp.qlen;
+        c.qsmall = c.tlen >= sp.qlen;
+        c.prof = prof + (c.qsmall ? qu.rev_off : qu.fwd_off);
+        c.S = profile_stride(sp.qlen);
+        int64_t cells = 0;
+        const int32_t s = align_pair(c, sp, (uint64_t)d, lane, cells, nullptr);
+        if (lane == 0) {
+            scores[d] = s;
+            if (cells_out) cells_out[d] = cells;
+        }
+    }
+}
+
 size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
 
 // Both profiles share one launch when they fit twice per SM with room to spare.
@@ -302,8 +340,18 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kWarpsPerCta * 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores,
-                                                                        d_cells);
+        if (kp.s.mode == HS_MODE_FULL) {
+            e = cudaFuncSetAttribute(scan_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_full_kernel, kWarpsPerCta * 32, smem);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            scan_full_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s,
+                                                                                 ws.scores, d_cells);
+        } else {
+            scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores,
+                                                                            d_cells);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         nl++;
@@ -516,7 +564,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
             best = again = ra.hit_score[slot];      // below the reporting threshold: no alignment
         } else {
             best = align_pair(c, sp, (uint64_t)d, lane, cells, &br);
-            again = align_round<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span);
+            again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span)
+                                            : align_round<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span);
         }
         if (lane == 0) {
             if (again != best || (ra.hit_score && ra.hit_score[slot] != best)) set_status(ra.status, HS_EINTERNAL);

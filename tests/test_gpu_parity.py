@@ -213,3 +213,51 @@ def test_swissprot_scale_sampled():
         s, oq, ot, _, _ = O.align_pair(q, t, M, op, 1, int(h["db_index"]))
         assert s == h["score"] and np.array_equal(rq, oq) and np.array_equal(rt, ot)
     D.close()
+
+
+def oparams_full(p: P.Params):
+    op = oparams(p)
+    op.mode = O.MODE_FULL
+    return op
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_full_slide_mode(case):
+    """Fig. 1 as printed (pair-wise form): every score, cell count, ranked
+    hit and alignment equals the oracle's, overhanging pieces included."""
+    rng = np.random.default_rng(4200 + case)
+    qlen = [1, 7, 40, 130, 300, 700][case]
+    lengths = np.concatenate([rng.integers(0, 4, 5), synth.lognormal_lengths(rng, 250, 150, 0.7, 1, 2500)])
+    db = synth.db_from_lengths(rng, lengths)
+    q = synth.residues(rng, qlen)
+    p = P.Params(pgp=int(rng.integers(0, 3)), gop=int(rng.integers(1, 15)), gep=int(rng.integers(0, 6)),
+                 rounds=[1, 20, 3, 20, 2, 5][case], lfactor_q16=int(rng.integers(20000, 65537)),
+                 sfactor_q16=int(rng.integers(20000, 65537)), minfactor_q16=int(rng.integers(0, 40000)),
+                 matrix=None if case % 2 else synth.random_symmetric_matrix(rng, -7, 9))
+    M = O.blosum62() if p.matrix is None else p.matrix
+    op = oparams_full(p)
+    seed = int(rng.integers(0, 2**62))
+    D = P.Database(db.codes, db.offsets)
+    hits, ops, scores, cells = run_device(D, q, 15, p_full(p), seed)
+    ref, ref_cells, _ = O.search_scores(db.codes, db.offsets, q, M, op, seed)
+    assert np.array_equal(scores, ref)
+    assert np.array_equal(cells, ref_cells)
+    check_hits(db, q, M, op, seed, hits, ops, ref, min(15, db.n))
+    s, o, _ = P.get_alignment(D, q, int(hits[0]["db_index"]), p_full(p), seed)
+    assert s == hits[0]["score"]
+    D.close()
+
+
+def p_full(p: P.Params):
+    f = P.Params(**p.__dict__)
+    f.mode = 1
+    return f
+
+
+def test_batched_rejects_full_mode():
+    rng = np.random.default_rng(1)
+    db = synth.db_from_lengths(rng, [50, 60])
+    D = P.Database(db.codes, db.offsets)
+    with pytest.raises(P.HsError):
+        P.search_batch(D, [synth.residues(rng, 10)], 2, p_full(P.Params()))
+    D.close()
