@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per serving rate (max)")
+    ap.add_argument("--bimodal", action="store_true",
+                    help="also time the load-balance workload under both schedules")
     return ap.parse_args()
 
 
@@ -305,6 +307,50 @@ def serving_section(P, D, db, params, max_requests, rates=(50.0, 200.0, 1000.0))
 
 
 # --------------------------------------------------------------------------
+# load balance: 16 queries (6x50, 5x500, 5x2000) against 100k targets, 90%
+# of 50-150 letters and 10% of 5,000-35,000, top-50, under the length-binned
+# schedule and in database order (same results, different balance)
+# --------------------------------------------------------------------------
+def bimodal_section(P):
+    import torch
+
+    from paper_1508_06561_gb300 import synth
+    db, queries, k = synth.bimodal(4)
+    D = P.Database(db.codes, db.offsets)
+    out = {"workload": "bimodal-100k-16q", "residues": int(db.residues), "n_seqs": int(db.n), "k": k}
+    st = torch.cuda.Stream()
+    qd = [torch.from_numpy(q).cuda() for q in queries]
+    longest = int(np.argmax([len(q) for q in queries]))
+    for name, sched in (("length_binned", P.Database.SCHEDULE_LENGTH), ("input_order", P.Database.SCHEDULE_INPUT)):
+        D.set_schedule(sched)
+        with torch.cuda.stream(st):
+            o1 = P.search_device(D, qd[longest], k, stream=st)
+            ws = o1["workspace"]
+            for q in qd:
+                P.search_device(D, q, k, stream=st, workspace=ws, out=o1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            per = []
+            for q in qd:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                P.search_device(D, q, k, stream=st, workspace=ws, out=o1)
+                e1.record(st)
+                per.append((len(q), e0, e1))
+            b.record(st)
+        st.synchronize()
+        t = a.elapsed_time(b) / 1000.0
+        by_len = {}
+        for L, e0, e1 in per:
+            by_len.setdefault(int(L), []).append(e0.elapsed_time(e1))
+        out[name] = {"value": len(qd) * db.residues / t, "unit": UNIT, "ms_total": t * 1000.0,
+                     "ms_per_query_by_qlen": {str(L): float(np.mean(v)) for L, v in sorted(by_len.items())}}
+    out["binned_speedup"] = out["input_order"]["ms_total"] / out["length_binned"]["ms_total"]
+    D.close()
+    return out
+
+
+# --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
@@ -432,6 +478,7 @@ def run_ours(args, world, rank, local):
         batched = batched_section(P, D, db, params, args.seed)
     if world == 1 and not args.no_serving and args.workload == "plain-large":
         serving = serving_section(P, D, db, params, args.serve_requests)
+    bimodal = bimodal_section(P) if (world == 1 and args.bimodal) else None
     cpu_rate, cpu_threads, ns, nres, tcpu = oracle_rate(db, q, args.seed, args.cpu_budget_s) \
         if world == 1 else (None, None, 0, 0, 0.0)
     line = {
@@ -451,6 +498,8 @@ def run_ours(args, world, rank, local):
         line["batched"] = batched
     if serving is not None:
         line["serving"] = serving
+    if bimodal is not None:
+        line["bimodal"] = bimodal
     if cpu_rate is not None:
         line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                                 "sample": "%d random sequences (%d residues) of the same database, scores only, "

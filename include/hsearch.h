@@ -123,6 +123,14 @@ int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs,
 int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, int64_t index_base,
                      void *stream, hs_db **out);
 
+/* Work schedule of the scan (results never depend on it).
+ * HS_SCHEDULE_LENGTH (the default after loading): longest targets first,
+ * targets of >= 2048 letters one per warp -- the length-binned layout.
+ * HS_SCHEDULE_INPUT: database order, for comparing load balance. */
+#define HS_SCHEDULE_LENGTH 0
+#define HS_SCHEDULE_INPUT  1
+int hs_db_set_schedule(hs_db *db, int32_t schedule, void *stream);
+
 /* The global index of a database's first sequence (0 unless a shard). */
 int hs_db_index_base(const hs_db *db, int64_t *index_base);
 

@@ -102,6 +102,13 @@ class Database:
             raise ValueError("database closed")
         return self._h
 
+    SCHEDULE_LENGTH, SCHEDULE_INPUT = 0, 1
+
+    def set_schedule(self, schedule: int, stream=None):
+        """Scan order: SCHEDULE_LENGTH (longest first, the default) or
+        SCHEDULE_INPUT (database order).  Results do not depend on it."""
+        check(lib().hs_db_set_schedule(self.handle, schedule, _stream_ptr(stream)), "hs_db_set_schedule")
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().hs_db_free(self._h)

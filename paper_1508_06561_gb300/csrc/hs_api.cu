@@ -127,8 +127,10 @@ struct hs_db {
     uint8_t *d_codes = nullptr;
     int64_t *d_offsets = nullptr;
     int32_t *d_order = nullptr;
-    int64_t *d_cumres = nullptr;            // residues before each position of the length order
-    std::vector<int32_t> sorted_len;        // lengths in scheduling order (non-increasing)
+    int64_t *d_cumres = nullptr;            // residues before each position of the schedule
+    std::vector<int32_t> lens;              // lengths in database order
+    std::vector<int32_t> sorted_len;        // lengths in schedule order (non-increasing unless input order)
+    int32_t schedule = HS_SCHEDULE_LENGTH;
     // host-API state (grown on demand)
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
@@ -249,31 +251,46 @@ int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seq
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->device);
     if (e != cudaSuccess) { hs_db_free(db); return from_cuda(e); }
 
-    // scheduling order: longest first, ties by index (results never depend on it)
-    std::vector<int32_t> order((size_t)n_seqs);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
-    });
-    db->sorted_len.resize((size_t)n_seqs);
-    std::vector<int64_t> cumres((size_t)n_seqs + 1, 0);
-    for (int64_t i = 0; i < n_seqs; i++) {
-        db->sorted_len[i] = (int32_t)(offsets[order[i] + 1] - offsets[order[i]]);
-        cumres[i + 1] = cumres[i] + db->sorted_len[i];
-    }
+    db->lens.resize((size_t)n_seqs);
+    for (int64_t i = 0; i < n_seqs; i++) db->lens[i] = (int32_t)(offsets[i + 1] - offsets[i]);
 
     e = cudaMalloc(&db->d_codes, (size_t)nres + kCodesPad);
     if (e == cudaSuccess) e = cudaMalloc(&db->d_offsets, sizeof(int64_t) * (size_t)(n_seqs + 1));
     if (e == cudaSuccess) e = cudaMalloc(&db->d_order, sizeof(int32_t) * (size_t)std::max<int64_t>(n_seqs, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&db->d_cumres, sizeof(int64_t) * (size_t)(n_seqs + 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(db->d_codes + nres, 0, kCodesPad, st);
     if (e == cudaSuccess && nres > 0) e = cudaMemcpyAsync(db->d_codes, codes, (size_t)nres, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_offsets, offsets, sizeof(int64_t) * (size_t)(n_seqs + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && n_seqs > 0) e = cudaMemcpyAsync(db->d_order, order.data(), sizeof(int32_t) * (size_t)n_seqs, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMalloc(&db->d_cumres, sizeof(int64_t) * (size_t)(n_seqs + 1));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_cumres, cumres.data(), sizeof(int64_t) * (size_t)(n_seqs + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { hs_db_free(db); return from_cuda(e); }
+    const int rc = hs_db_set_schedule(db, HS_SCHEDULE_LENGTH, stream);
+    if (rc != HS_OK) { hs_db_free(db); return rc; }
     *out = db;
+    return HS_OK;
+}
+
+int hs_db_set_schedule(hs_db *db, int32_t schedule, void *stream)
+{
+    if (!db || (schedule != HS_SCHEDULE_LENGTH && schedule != HS_SCHEDULE_INPUT)) return HS_EINVAL;
+    const int64_t n = db->n;
+    // the schedule: longest first (ties by index), or database order
+    std::vector<int32_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    if (schedule == HS_SCHEDULE_LENGTH)
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return db->lens[a] > db->lens[b]; });
+    db->sorted_len.resize((size_t)n);
+    std::vector<int64_t> cumres((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; i++) {
+        db->sorted_len[i] = db->lens[order[i]];
+        cumres[i + 1] = cumres[i] + db->sorted_len[i];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (n > 0) e = cudaMemcpyAsync(db->d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_cumres, cumres.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    db->schedule = schedule;
     return HS_OK;
 }
 
@@ -345,10 +362,13 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
     }
     if (db->n == 0) return HS_OK;
 
-    // role split and the long prefix in the length order
+    // role split and the long prefix in the length order (unused in input order)
     const auto &L = db->sorted_len;
-    const int64_t split = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= qlen; }) - L.begin();
-    const int64_t long_end = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
+    const bool input_order = db->schedule == HS_SCHEDULE_INPUT;
+    const int64_t split = input_order ? 0 :
+        std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= qlen; }) - L.begin();
+    const int64_t long_end = input_order ? 0 :
+        std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
     DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
     ScanTrace tr{nullptr, nullptr};
     if (db->trace) {
@@ -357,7 +377,7 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
     }
     int launches = 0;
     e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st, db->trace ? &tr : nullptr,
-                    &launches);
+                    &launches, input_order);
     if (e == cudaSuccess && d_count)
         e = launch_count_at_least(ws.scores, db->n, min_score, d_count, db->num_sms, st, &launches);
     if (e == cudaSuccess && nhits > 0) e = launch_topk(ws, db->n, nhits, st, &launches);
@@ -605,7 +625,8 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     if (db->n == 0 || nq == 0) return HS_OK;
 
     const auto &L = db->sorted_len;
-    const int64_t long_end = std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
+    const int64_t long_end = db->schedule == HS_SCHEDULE_INPUT ? 0 :
+        std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
     DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
     ScanTrace tr{nullptr, nullptr};
     if (db->trace) {

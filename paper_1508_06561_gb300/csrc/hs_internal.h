@@ -108,7 +108,7 @@ struct ScanTrace {
 };
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
-                        cudaStream_t st, const ScanTrace *trace, int *launches);
+                        cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order);
 size_t scan_smem_bytes(int32_t qlen);
 cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches);
 cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32_t nhits, cudaStream_t st,

@@ -233,7 +233,9 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ Plan plans[kWarpsPerCta][32];
-    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    // profiles in shared memory, or read in place from global memory when
+    // nothing is staged (input-order schedule with long queries)
+    const uint32_t *prof = qu.smem_words ? reinterpret_cast<const uint32_t *>(smem_raw) : prof_g;
     {
         const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
         const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
@@ -262,7 +264,7 @@ scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, S
         for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
     }
     __syncthreads();
-    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    const uint32_t *prof = qu.smem_words ? reinterpret_cast<const uint32_t *>(smem_raw) : prof_g;
     const int lane = threadIdx.x & 31;
     for (;;) {
         long long pos = 0;
@@ -294,7 +296,7 @@ static bool fuse_roles(int32_t qlen) { return 2 * scan_smem_bytes(qlen) <= 100 *
 
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
-                        cudaStream_t st, const ScanTrace *trace, int *launches)
+                        cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order)
 {
     const int64_t words = profile_words(kp.s.qlen);
     ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof};
@@ -306,7 +308,15 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
     ScanQueue qs[2];
     const uint32_t *srcs[2];
     int nq = 0;
-    if (fuse_roles(kp.s.qlen)) {
+    if (input_order) {
+        // one queue in database order, roles mixed, no long-target phase
+        ScanQueue &q = qs[nq];
+        q.begin = 0; q.end = db.n; q.long_end = 0;
+        q.ctr = ws.counters + kQsLong;
+        q.smem_words = fuse_roles(kp.s.qlen) ? 2 * words : 0;
+        q.rev_off = 0; q.fwd_off = (int)words;
+        srcs[nq++] = ws.prof;
+    } else if (fuse_roles(kp.s.qlen)) {
         ScanQueue &q = qs[nq];
         q.begin = 0; q.end = db.n; q.long_end = min(long_end, split);
         q.ctr = ws.counters + kQsLong;
