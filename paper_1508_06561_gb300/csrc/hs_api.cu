@@ -112,6 +112,7 @@ static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams
     sp.index_base = 0;
     sp.min_score = INT_MIN;
     sp.mode = p->mode;
+    sp.pair16 = (int64_t)range * (qlen + 3) <= 65535;
     return HS_OK;
 }
 
@@ -638,7 +639,7 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     launches++;
     if (e == cudaSuccess)
         e = launch_scan_batch(v, db->d_cumres, long_end, kp, bl, nchunk, ctas_per_sm, db->num_sms, st,
-                              db->trace ? &tr : nullptr, &launches);
+                              db->trace ? &tr : nullptr, &launches, db->schedule == HS_SCHEDULE_INPUT);
     if (e == cudaSuccess && nhits > 0) e = launch_topk_batch(bl, db->n, k, nhits, st, &launches);
     if (e == cudaSuccess && nhits > 0)
         e = launch_replay_batch(v, kp, bl, nhits, k, d_hits, d_ops, ops_cap, d_ops_used, d_status, st, &launches);

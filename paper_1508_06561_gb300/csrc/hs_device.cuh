@@ -103,17 +103,52 @@ __device__ __forceinline__ uint32_t profile_word_value(const uint8_t *q, int qle
 // Byte lanes hold biased cells (M+bias >= 0); they are widened into 32-bit
 // sums every `flush` iterations, before any byte can overflow.
 // ---------------------------------------------------------------------------
-struct Acc4 {
+// Widened sums of a chunk's 4 shifts.  Acc<false>: four 32-bit sums.
+// Acc<true>: two registers of two 16-bit sums each (byte w goes to half w%2
+// of register w/2 by one byte permute), used when no shift's biased sum can
+// reach 65536: range * (qlen + 3) <= 65535, true for BLOSUM62 at any query
+// length the library accepts.
+template <bool P16> struct Acc;
+
+template <> struct Acc<false> {
     uint32_t a0, a1, a2, a3;
+    __device__ __forceinline__ void zero() { a0 = a1 = a2 = a3 = 0; }
+    __device__ __forceinline__ void add(uint32_t x)
+    {
+        a0 += x & 0xFFu;
+        a1 += (x >> 8) & 0xFFu;
+        a2 += (x >> 16) & 0xFFu;
+        a3 += x >> 24;
+    }
+    __device__ __forceinline__ void xor_reduce(int o)
+    {
+        a0 += __shfl_xor_sync(0xFFFFFFFFu, a0, o);
+        a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, o);
+        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+        a3 += __shfl_xor_sync(0xFFFFFFFFu, a3, o);
+    }
+    __device__ __forceinline__ uint32_t get(int w) const { return w == 0 ? a0 : w == 1 ? a1 : w == 2 ? a2 : a3; }
 };
 
-__device__ __forceinline__ void spread(uint32_t x, Acc4 &A)
-{
-    A.a0 += x & 0xFFu;
-    A.a1 += (x >> 8) & 0xFFu;
-    A.a2 += (x >> 16) & 0xFFu;
-    A.a3 += x >> 24;
-}
+template <> struct Acc<true> {
+    uint32_t p01, p23;
+    __device__ __forceinline__ void zero() { p01 = p23 = 0; }
+    __device__ __forceinline__ void add(uint32_t x)
+    {
+        p01 += __byte_perm(x, 0u, 0x4140);   // bytes 0, 1 -> halves 0, 1
+        p23 += __byte_perm(x, 0u, 0x4342);   // bytes 2, 3 -> halves 0, 1
+    }
+    __device__ __forceinline__ void xor_reduce(int o)
+    {
+        p01 += __shfl_xor_sync(0xFFFFFFFFu, p01, o);
+        p23 += __shfl_xor_sync(0xFFFFFFFFu, p23, o);
+    }
+    __device__ __forceinline__ uint32_t get(int w) const
+    {
+        const uint32_t r = w < 2 ? p01 : p23;
+        return (w & 1) ? r >> 16 : r & 0xFFFFu;
+    }
+};
 
 // bytes w with w <= p and p - w < ss
 __device__ __forceinline__ uint32_t edge_mask(int p, int ss)
@@ -127,20 +162,22 @@ __device__ __forceinline__ uint32_t edge_mask(int p, int ss)
 // Query-small iterations p in [pa, pb) of a chunk: letter tl[p], stored
 // column sbase - p.  pw = prof + sbase - pa, so iteration p reads
 // pw[tl[p] * R - (p - pa)].
+template <bool P16>
 __device__ __forceinline__ void rev_masked(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
-                                           int pa, int pb, int flush, Acc4 &A)
+                                           int pa, int pb, int flush, Acc<P16> &A)
 {
     uint32_t x = 0;
     int n = 0;
     for (int p = pa; p < pb; p++) {
         x += prof[tl[p] * R + sbase - p] & edge_mask(p, ss);
-        if (++n == flush) { spread(x, A); x = 0; n = 0; }
+        if (++n == flush) { A.add(x); x = 0; n = 0; }
     }
-    spread(x, A);
+    A.add(x);
 }
 
+template <bool P16>
 __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int pa,
-                                         int pb, int flush, Acc4 &A)
+                                         int pb, int flush, Acc<P16> &A)
 {
     const uint32_t *pw = prof + (sbase - pa);
     const uint8_t *tp = tl + pa;
@@ -154,8 +191,8 @@ __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint
             y += pw[tp[i + 1] * R - (i + 1)];
         }
         if (i < ce) x += pw[tp[i] * R - i];
-        spread(x, A);
-        spread(y, A);
+        A.add(x);
+        A.add(y);
     }
 }
 
@@ -163,11 +200,12 @@ __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint
 // The segment's first 3 and last 3 iterations run with byte masks: partial
 // ones where the segment holds the range's first (p < 3) or last (p >= ss)
 // iterations, all-ones elsewhere -- the same instructions on every lane.
+template <bool P16>
 __device__ __forceinline__ void rev_segment(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
-                                            int it0, int it1, bool first, bool last, int flush, Acc4 &A)
+                                            int it0, int it1, bool first, bool last, int flush, Acc<P16> &A)
 {
     if (ss < 3) {                                   // edges overlap: mask every iteration
-        rev_masked(prof, R, tl, sbase, ss, it0, it1, flush, A);
+        rev_masked<P16>(prof, R, tl, sbase, ss, it0, it1, flush, A);
         return;
     }
     const uint32_t f0 = first ? 0x000000FFu : ~0u, f1 = first ? 0x0000FFFFu : ~0u, f2 = first ? 0x00FFFFFFu : ~0u;
@@ -181,19 +219,20 @@ __device__ __forceinline__ void rev_segment(const uint32_t *prof, int R, const u
     const uint32_t b1 = pw[tl[e + 1] * R - (e + 1)] & l1;
     const uint32_t b2 = pw[tl[e + 2] * R - (e + 2)] & l2;
     if (flush >= 3) {
-        spread(a0 + a1 + a2, A);
-        spread(b0 + b1 + b2, A);
+        A.add(a0 + a1 + a2);
+        A.add(b0 + b1 + b2);
     } else {
-        spread(a0, A); spread(a1, A); spread(a2, A);
-        spread(b0, A); spread(b1, A); spread(b2, A);
+        A.add(a0); A.add(a1); A.add(a2);
+        A.add(b0); A.add(b1); A.add(b2);
     }
-    if (it0 + 3 < e) rev_main(prof, R, tl, sbase, it0 + 3, e, flush, A);
+    if (it0 + 3 < e) rev_main<P16>(prof, R, tl, sbase, it0 + 3, e, flush, A);
 }
 
 // iterations [it0, it1) of a query-large chunk: letter ts[j], stored column
 // s0 + j (no edges)
+template <bool P16>
 __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uint8_t *ts, int s0, int it0, int it1,
-                                          int flush, Acc4 &A)
+                                          int flush, Acc<P16> &A)
 {
     const uint32_t *pw = prof + (s0 + it0);
     const uint8_t *tp = ts + it0;
@@ -207,8 +246,8 @@ __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uin
             y += pw[tp[i + 1] * R + i + 1];
         }
         if (i < ce) x += pw[tp[i] * R + i];
-        spread(x, A);
-        spread(y, A);
+        A.add(x);
+        A.add(y);
     }
 }
 
@@ -219,12 +258,13 @@ __device__ __forceinline__ void lane_best1(uint32_t acc, int k, int nshift, int3
 }
 
 // shifts ascend within a chunk, so a strict '>' keeps the lowest k
-__device__ __forceinline__ void lane_best(const Acc4 &A, int k0, int nshift, int32_t off, int32_t &bv, int32_t &bk)
+template <bool P16>
+__device__ __forceinline__ void lane_best(const Acc<P16> &A, int k0, int nshift, int32_t off, int32_t &bv, int32_t &bk)
 {
-    lane_best1(A.a0, k0, nshift, off, bv, bk);
-    lane_best1(A.a1, k0 + 1, nshift, off, bv, bk);
-    lane_best1(A.a2, k0 + 2, nshift, off, bv, bk);
-    lane_best1(A.a3, k0 + 3, nshift, off, bv, bk);
+    lane_best1(A.get(0), k0, nshift, off, bv, bk);
+    lane_best1(A.get(1), k0 + 1, nshift, off, bv, bk);
+    lane_best1(A.get(2), k0 + 2, nshift, off, bv, bk);
+    lane_best1(A.get(3), k0 + 3, nshift, off, bv, bk);
 }
 
 __device__ __forceinline__ void warp_argmax(int32_t bv, int32_t bk, int32_t &vmax, int32_t &kstar)
@@ -263,8 +303,9 @@ __device__ __forceinline__ void plan_grid(Plan &g)
 // The whole warp scans one step (lane grid from plan_grid).  Byte sums of a
 // chunk's segments are added across its Gj lanes by shuffles; the best
 // (V, k) pair over all chunks comes from two warp reductions.
-__device__ __forceinline__ void coop_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
-                                          int flush, int lane, int32_t &vmax, int32_t &kstar)
+template <bool P16>
+__device__ __forceinline__ void coop_scan_t(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
+                                            int flush, int lane, int32_t &vmax, int32_t &kstar)
 {
     const int nshift = g.ls - g.ss + 1;
     const int niter = g.qsmall ? g.ss + 3 : g.ss;
@@ -279,39 +320,51 @@ __device__ __forceinline__ void coop_scan(const uint32_t *prof, int R, int qlen,
     for (int base = 0; base < nshift; base += 4 * Gk) {
         const int k0 = base + 4 * gk;
         const bool live = in_grid && k0 < nshift;
-        Acc4 A = {0u, 0u, 0u, 0u};
+        Acc<P16> A;
+        A.zero();
         if (live) {
             if (g.qsmall)
-                rev_segment(prof, R, g.t + g.Lp + k0, sbase, g.ss, it0, it1, gj == 0, gj == Gj - 1, flush, A);
+                rev_segment<P16>(prof, R, g.t + g.Lp + k0, sbase, g.ss, it0, it1, gj == 0, gj == Gj - 1, flush, A);
             else
-                fwd_chunk(prof, R, g.t + g.Sp, g.Lp + k0 + 4, it0, it1, flush, A);
+                fwd_chunk<P16>(prof, R, g.t + g.Sp, g.Lp + k0 + 4, it0, it1, flush, A);
         }
-        for (int o = 1; o < Gj; o <<= 1) {
-            A.a0 += __shfl_xor_sync(0xFFFFFFFFu, A.a0, o);
-            A.a1 += __shfl_xor_sync(0xFFFFFFFFu, A.a1, o);
-            A.a2 += __shfl_xor_sync(0xFFFFFFFFu, A.a2, o);
-            A.a3 += __shfl_xor_sync(0xFFFFFFFFu, A.a3, o);
-        }
+        for (int o = 1; o < Gj; o <<= 1) A.xor_reduce(o);
         if (live && gj == 0) lane_best(A, k0, nshift, off, bv, bk);
     }
     warp_argmax(bv, bk, vmax, kstar);
 }
 
+__device__ __forceinline__ void coop_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
+                                          int flush, bool pair16, int lane, int32_t &vmax, int32_t &kstar)
+{
+    if (pair16) coop_scan_t<true>(prof, R, qlen, g, bias, flush, lane, vmax, kstar);
+    else coop_scan_t<false>(prof, R, qlen, g, bias, flush, lane, vmax, kstar);
+}
+
 // One lane scans a whole step alone, chunk after chunk.
-__device__ __forceinline__ void lane_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
-                                          int flush, int32_t &vmax, int32_t &kstar)
+template <bool P16>
+__device__ __forceinline__ void lane_scan_t(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
+                                            int flush, int32_t &vmax, int32_t &kstar)
 {
     const int nshift = g.ls - g.ss + 1;
     const int32_t off = bias * g.ss;
     int32_t bv = INT_MIN, bk = INT_MAX;
     for (int k0 = 0; k0 < nshift; k0 += 4) {
-        Acc4 A = {0u, 0u, 0u, 0u};
-        if (g.qsmall) rev_segment(prof, R, g.t + g.Lp + k0, qlen + 3 - g.Sp, g.ss, 0, g.ss + 3, true, true, flush, A);
-        else fwd_chunk(prof, R, g.t + g.Sp, g.Lp + k0 + 4, 0, g.ss, flush, A);
+        Acc<P16> A;
+        A.zero();
+        if (g.qsmall) rev_segment<P16>(prof, R, g.t + g.Lp + k0, qlen + 3 - g.Sp, g.ss, 0, g.ss + 3, true, true, flush, A);
+        else fwd_chunk<P16>(prof, R, g.t + g.Sp, g.Lp + k0 + 4, 0, g.ss, flush, A);
         lane_best(A, k0, nshift, off, bv, bk);
     }
     vmax = bv;
     kstar = bk;
+}
+
+__device__ __forceinline__ void lane_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
+                                          int flush, bool pair16, int32_t &vmax, int32_t &kstar)
+{
+    if (pair16) lane_scan_t<true>(prof, R, qlen, g, bias, flush, vmax, kstar);
+    else lane_scan_t<false>(prof, R, qlen, g, bias, flush, vmax, kstar);
 }
 
 // ---------------------------------------------------------------------------
@@ -384,7 +437,7 @@ __device__ __forceinline__ int32_t align_round(const PairCtx &c, const SParams &
         int32_t vmax, kstar;
         Plan g = {c.t, Lp, Sp, ls, ss, c.qsmall ? 1 : 0, 0, 0, 0};
         plan_grid(g);
-        coop_scan(c.prof, c.S, c.qlen, g, kp.bias, kp.flush, lane, vmax, kstar);
+        coop_scan(c.prof, c.S, c.qlen, g, kp.bias, kp.flush, kp.pair16 != 0, lane, vmax, kstar);
         cells += (int64_t)(ls - ss + 1) * ss;
         int32_t gap = 0;
         if (kstar > 0) gap = (t == 0) ? kp.pgp * kstar : kp.gop + (kstar - 1) * kp.gep;

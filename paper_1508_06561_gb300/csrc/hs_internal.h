@@ -35,6 +35,7 @@ struct SParams {
     int64_t index_base;                 // database index of the first loaded sequence (shards)
     int32_t min_score;                  // replay only hits scoring >= this (threshold search)
     int32_t mode;                       // HS_MODE_DB or HS_MODE_FULL
+    int32_t pair16;                     // 16-bit chunk sums suffice: (max-min) * (qlen+3) <= 65535
 };
 
 // The matrix (for building profiles) plus the scoring parameters.
@@ -116,7 +117,7 @@ cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32
 cudaError_t launch_prof_offsets(const BatchLayout &bl, cudaStream_t st);
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
                               const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
-                              cudaStream_t st, const ScanTrace *trace, int *launches);
+                              cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order);
 cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const BatchLayout &bl, int32_t nhits,
                                 int32_t k, hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
                                 int32_t *d_status, cudaStream_t st, int *launches);

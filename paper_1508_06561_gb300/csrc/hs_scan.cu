@@ -127,6 +127,7 @@ struct PosQueue {
     unsigned *ctr;                  // global or shared counter of handed-out positions
 };
 
+template <bool P16>
 __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, const QueryCtx &qc,
                                           const PosQueue &qu, Plan *plans, int lane)
 {
@@ -185,7 +186,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             const int64_t iters = (int64_t)((ls - g.ss + 4) >> 2) * (g.ss + (L.qsmall ? 3 : 0));
             local = iters <= kLocalIters;
             if (local) {
-                lane_scan(L.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, g, sp.bias, sp.flush, vmax, kstar);
+                lane_scan_t<P16>(L.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, g, sp.bias, sp.flush, vmax, kstar);
             } else {
                 plan_grid(g);
                 plans[lane] = g;
@@ -199,7 +200,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             coop &= coop - 1;
             const Plan h = plans[i];
             int32_t v, k;
-            coop_scan(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
+            coop_scan_t<P16>(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
             if (lane == i) { vmax = v; kstar = k; }
         }
         // consume (Fig. 1: delete the used-up parts) and score incrementally (A17)
@@ -227,44 +228,58 @@ struct ScanQueue {
     int rev_off, fwd_off;           // word offsets of the two role profiles
 };
 
+// kSmem: the profiles are staged in shared memory (known to the compiler, so
+// every profile read is a shared load); otherwise they are read in place from
+// global memory (database-order schedule with a query too long for both
+// roles to fit).  P16: 16-bit chunk sums (SParams::pair16).
+template <bool kSmem, bool P16>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
 scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
             int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ Plan plans[kWarpsPerCta][32];
-    // profiles in shared memory, or read in place from global memory when
-    // nothing is staged (input-order schedule with long queries)
-    const uint32_t *prof = qu.smem_words ? reinterpret_cast<const uint32_t *>(smem_raw) : prof_g;
-    {
+    const uint32_t *prof = prof_g;
+    if (kSmem) {
         const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
         const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
         for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+        __syncthreads();
+        prof = reinterpret_cast<const uint32_t *>(smem_raw);
     }
-    __syncthreads();
     QueryCtx qc;
     qc.prof_rev = prof + qu.rev_off;
     qc.prof_fwd = prof + qu.fwd_off;
     qc.scores = scores;
     qc.cells = cells_out;
     const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
-    run_pairs(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+}
+
+typedef void (*ScanKernelFn)(DbView, ScanQueue, const uint32_t *, SParams, int32_t *, int64_t *);
+
+static ScanKernelFn pick_scan_kernel(bool smem, bool p16)
+{
+    if (smem) return p16 ? scan_kernel<true, true> : scan_kernel<true, false>;
+    return p16 ? scan_kernel<false, true> : scan_kernel<false, false>;
 }
 
 // Full-slide mode (pair-wise form): one warp per pair, pairs taken one at a
 // time from the same longest-first queue; the pair's state is warp-uniform.
+template <bool kSmem>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
                  int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
     extern __shared__ uint4 smem_raw[];
-    {
+    const uint32_t *prof = prof_g;
+    if (kSmem) {
         const int64_t n16 = qu.smem_words / 4;
         const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
         for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+        __syncthreads();
+        prof = reinterpret_cast<const uint32_t *>(smem_raw);
     }
-    __syncthreads();
-    const uint32_t *prof = qu.smem_words ? reinterpret_cast<const uint32_t *>(smem_raw) : prof_g;
     const int lane = threadIdx.x & 31;
     for (;;) {
         long long pos = 0;
@@ -344,23 +359,18 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
     }
     for (int i = 0; i < nq; i++) {
         const size_t smem = (size_t)qs[i].smem_words * 4;
-        e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const bool staged = qs[i].smem_words > 0;
+        const ScanKernelFn kern = kp.s.mode == HS_MODE_FULL
+                                      ? (staged ? scan_full_kernel<true> : scan_full_kernel<false>)
+                                      : pick_scan_kernel(staged, kp.s.pair16 != 0);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kWarpsPerCta * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerCta * 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        if (kp.s.mode == HS_MODE_FULL) {
-            e = cudaFuncSetAttribute(scan_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_full_kernel, kWarpsPerCta * 32, smem);
-            if (e != cudaSuccess) return e;
-            if (per_sm < 1) return cudaErrorInvalidConfiguration;
-            scan_full_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s,
-                                                                                 ws.scores, d_cells);
-        } else {
-            scan_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores,
-                                                                            d_cells);
+        {
+            kern<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores, d_cells);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -412,6 +422,11 @@ struct BatchScan {
     unsigned *item_ctr;
 };
 
+// kSmem (length order): a chunk that straddles its query's role switch is run
+// as two sub-ranges, each with its role's profile staged, so every profile
+// read is a shared load.  Otherwise (database order, roles mixed) both role
+// profiles are read from global memory.
+template <bool kSmem, bool P16>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 2)
 scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
 {
@@ -436,32 +451,61 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
             SParams sp = sp0;
             sp.qlen = (int32_t)(bs.qoffsets[q + 1] - bs.qoffsets[q]);
             sp.seed = bs.seeds[q];
-            const int64_t d0 = db.order[b0];
-            const int role = (db.offsets[d0 + 1] - db.offsets[d0]) >= sp.qlen ? 0 : 1;
             const int64_t words = profile_words(sp.qlen);
             const uint32_t *pg = bs.prof + bs.prof_off[q];
-            if (q != cur_q || role != cur_role) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(pg + (role ? words : 0));
-                for (int64_t i = threadIdx.x; i < words / 4; i += blockDim.x) smem_raw[i] = src[i];
-                cur_q = q;
-                cur_role = role;
-            }
-            __syncthreads();
             QueryCtx qc;
-            qc.prof_rev = role == 0 ? prof_s : pg;
-            qc.prof_fwd = role == 1 ? prof_s : pg + words;
             qc.scores = bs.scores + (int64_t)q * db.n;
             qc.cells = nullptr;
-            const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
-            run_pairs(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+            if (kSmem) {
+                // first position of the chunk whose target is shorter than the
+                // query (targets are longest first)
+                int64_t lo = b0, hi = b1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1, d = db.order[mid];
+                    if (db.offsets[d + 1] - db.offsets[d] >= sp.qlen) lo = mid + 1;
+                    else hi = mid;
+                }
+                for (int role = 0; role < 2; role++) {
+                    const int64_t r0 = role ? lo : b0, r1 = role ? b1 : lo;
+                    if (r0 >= r1) continue;
+                    if (q != cur_q || role != cur_role) {
+                        __syncthreads();                    // the previous profile is no longer read
+                        const uint4 *src = reinterpret_cast<const uint4 *>(pg + (role ? words : 0));
+                        for (int64_t i = threadIdx.x; i < words / 4; i += blockDim.x) smem_raw[i] = src[i];
+                        cur_q = q;
+                        cur_role = role;
+                    }
+                    if (threadIdx.x == 0) s_pos = 0;
+                    __syncthreads();
+                    qc.prof_rev = prof_s;
+                    qc.prof_fwd = prof_s;
+                    const PosQueue pq = {r0, max(r0, min(bs.long_end, r1)), r1, &s_pos};
+                    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+                    __syncthreads();                        // all warps are done with s_pos
+                }
+            } else {
+                __syncthreads();
+                qc.prof_rev = pg;
+                qc.prof_fwd = pg + words;
+                const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
+                run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+            }
         }
         __syncthreads();
     }
 }
 
+typedef void (*BatchKernelFn)(DbView, BatchScan, SParams);
+
+static BatchKernelFn pick_batch_kernel(bool smem, bool p16)
+{
+    if (smem) return p16 ? scan_batch_kernel<true, true> : scan_batch_kernel<true, false>;
+    return p16 ? scan_batch_kernel<false, true> : scan_batch_kernel<false, false>;
+}
+
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
                               const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
-                              cudaStream_t st, const ScanTrace *trace, int *launches)
+                              cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order)
 {
     ProfileJob job = {bl.queries, bl.qoffsets, bl.prof_off, 0, bl.prof};
     profile_kernel<<<dim3(16, bl.nq), 256, 0, st>>>(job, kp);
@@ -481,11 +525,12 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
     bs.long_end = long_end;
     bs.scores = bl.scores;
     bs.item_ctr = bl.item_ctr;
-    const size_t smem = (size_t)profile_words(bl.max_qlen) * 4;
-    e = cudaFuncSetAttribute(scan_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const BatchKernelFn kern = pick_batch_kernel(!input_order, kp.s.pair16 != 0);
+    const size_t smem = input_order ? 0 : (size_t)profile_words(bl.max_qlen) * 4;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_batch_kernel, kWarpsPerCta * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerCta * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
@@ -493,7 +538,7 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         e = cudaEventRecord(trace->start, st);
         if (e != cudaSuccess) return e;
     }
-    scan_batch_kernel<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, bs, kp.s);
+    kern<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, bs, kp.s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (trace && trace->stop) {

@@ -20,4 +20,10 @@ using std::min; using std::max;
 inline int __reduce_max_sync(unsigned, int v) { return v; }
 inline int __reduce_min_sync(unsigned, int v) { return v; }
 template <class T> inline T __shfl_xor_sync(unsigned, T v, int) { return v; }
+// byte n of the result is byte (s >> 4n) & 7 of the 8-byte value y:x (x low)
+inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
+    uint64_t v = ((uint64_t)y << 32) | x; uint32_t r = 0;
+    for (int n = 0; n < 4; n++) r |= (uint32_t)((v >> (8 * ((s >> (4 * n)) & 7))) & 0xFF) << (8 * n);
+    return r;
+}
 inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }

@@ -4,6 +4,8 @@
 // segments, and every lane-local step must equal a naive sum of matrix
 // entries, and every profile/target read must stay inside its buffer: the
 // buffers end at PROT_NONE guard pages, so a stray read faults.
+// Both accumulator forms are checked: 32-bit sums always, 16-bit pair sums
+// whenever range * (qlen + 3) <= 65535 (the condition the library uses).
 // usage: lane_emu SEED [MIN MAX]   (matrix entries drawn from [MIN, MAX])
 #include <sys/mman.h>
 #include <unistd.h>
@@ -26,6 +28,30 @@ template <class T> T *guarded(size_t n, T **base_out) {
     *base_out = p;
     return p;
 }
+// one 4-shift chunk summed over nseg iteration segments into one accumulator;
+// returns the number of shifts checked, or -1 - x for a mismatch at shift k0 + x
+template <bool P16>
+long check_chunk(const uint32_t *prof, int R, int qlen, const uint8_t *t, int Lp, int Sp, int ss, bool qsmall,
+                 int k0, int nseg, int nshift, int flush, int bias, const std::vector<int> &V) {
+    int niter = qsmall ? ss + 3 : ss;
+    Acc<P16> A;
+    A.zero();
+    for (int sg = 0; sg < nseg; sg++) {
+        int it0 = sg * niter / nseg, it1 = (sg + 1) * niter / nseg;
+        if (qsmall) rev_segment<P16>(prof, R, t + Lp + k0, qlen + 3 - Sp, ss, it0, it1, sg == 0, sg == nseg - 1, flush, A);
+        else fwd_chunk<P16>(prof, R, t + Sp, Lp + k0 + 4, it0, it1, flush, A);
+    }
+    long n = 0;
+    for (int x = 0; x < 4 && k0 + x < nshift; x++, n++)
+        if ((int)A.get(x) - bias * ss != V[k0 + x]) return -1 - x;
+    return n;
+}
+template <bool P16>
+bool check_lane_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias, int flush, int bestv, int bestk) {
+    int32_t vm, ks;
+    lane_scan_t<P16>(prof, R, qlen, g, bias, flush, vm, ks);
+    return vm == bestv && ks == bestk;
+}
 int main(int argc, char **argv) {
     std::mt19937_64 rng(argc > 1 ? atoi(argv[1]) : 1);
     int8_t M[576];
@@ -44,6 +70,8 @@ int main(int argc, char **argv) {
         for (int i = 0; i < tlen; i++) t[i] = rng() % 24;
         memset(t + tlen, 0, kCodesPad);
         int R = profile_stride(qlen);
+        // 16-bit pair sums whenever the library would pick them
+        const bool p16 = (long)(hi - lo) * (qlen + 3) <= 65535;
         for (int rev = 0; rev < 2; rev++) {
             uint32_t *pb; uint32_t *prof = guarded<uint32_t>((size_t)profile_words(qlen), &pb);
             for (int a = 0; a < 24; a++) for (int s = 0; s < R; s++) prof[a * R + s] = profile_word_value(q.data(), qlen, rev, M, bias, a, s);
@@ -63,27 +91,21 @@ int main(int argc, char **argv) {
                 std::vector<int> V(nshift);
                 for (int k = 0; k < nshift; k++) { int v = 0; for (int j = 0; j < ss; j++) { int a = L[Lp+k+j], b = S[Sp+j]; v += qsmall ? M[b*24+a] : M[a*24+b]; } V[k] = v; if (v > bestv) { bestv = v; bestk = k; } }
                 // lane scan (whole step) and per-chunk segments with random splits
-                int32_t vm, ks;
                 if (nshift <= 64) {
-                    lane_scan(prof, R, qlen, g, bias, flush, vm, ks);
-                    if (vm != bestv || ks != bestk) { printf("lane_scan mismatch trial %d\n", trial); return 1; }
+                    if (!check_lane_scan<false>(prof, R, qlen, g, bias, flush, bestv, bestk) ||
+                        (p16 && !check_lane_scan<true>(prof, R, qlen, g, bias, flush, bestv, bestk))) {
+                        printf("lane_scan mismatch trial %d\n", trial); return 1;
+                    }
                 }
                 int niter = qsmall ? ss + 3 : ss;
                 for (int k0 = 0; k0 < nshift; k0 += 4) {
                     int nseg = 1 + rng() % 4;
                     int minseg = qsmall ? 6 : 4;
                     if (niter < nseg * minseg) nseg = 1;
-                    Acc4 A = {0, 0, 0, 0};
-                    for (int sg = 0; sg < nseg; sg++) {
-                        int it0 = sg * niter / nseg, it1 = (sg + 1) * niter / nseg;
-                        if (qsmall) rev_segment(prof, R, t + Lp + k0, qlen + 3 - Sp, ss, it0, it1, sg == 0, sg == nseg - 1, flush, A);
-                        else fwd_chunk(prof, R, t + Sp, Lp + k0 + 4, it0, it1, flush, A);
-                    }
-                    uint32_t acc[4] = {A.a0, A.a1, A.a2, A.a3};
-                    for (int x = 0; x < 4 && k0 + x < nshift; x++) {
-                        if ((int)acc[x] - bias * ss != V[k0 + x]) { printf("chunk mismatch trial %d k %d\n", trial, k0 + x); return 1; }
-                        checks++;
-                    }
+                    long c = check_chunk<false>(prof, R, qlen, t, Lp, Sp, ss, qsmall, k0, nseg, nshift, flush, bias, V);
+                    if (c >= 0 && p16) c = check_chunk<true>(prof, R, qlen, t, Lp, Sp, ss, qsmall, k0, nseg, nshift, flush, bias, V);
+                    if (c < 0) { printf("chunk mismatch trial %d k %ld\n", trial, k0 - 1 - c); return 1; }
+                    checks += c;
                 }
             }
         }
