@@ -59,6 +59,21 @@ __global__ void profile_kernel(ProfileJob job, KParams kp)
 // holds a pair) so each gets the warp alone.
 // ---------------------------------------------------------------------------
 constexpr int kLocalIters = 64;
+// flattened scan (16-bit pair sums): a step joins the unit list when it has
+// at least kFlatMinChunks chunks or at most kFlatMaxIters iterations per
+// chunk; the rest (few long chunks) get the warp's lane grid
+#ifndef HS_FLAT_MIN_CHUNKS
+#define HS_FLAT_MIN_CHUNKS 16
+#endif
+#ifndef HS_FLAT_MAX_ITERS
+#define HS_FLAT_MAX_ITERS 64
+#endif
+#ifndef HS_UNIT_SHIFTS
+#define HS_UNIT_SHIFTS 4
+#endif
+constexpr int kFlatMinChunks = HS_FLAT_MIN_CHUNKS;
+constexpr int kUnitShifts = HS_UNIT_SHIFTS;         // shifts per unit of the flattened list: 4 or 8
+constexpr int kFlatMaxIters = HS_FLAT_MAX_ITERS;
 
 struct QueryCtx {
     const uint32_t *prof_rev;       // profile for pairs where the query is the small sequence
@@ -173,9 +188,10 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         if (!open && __ballot_sync(0xFFFFFFFFu, busy) == 0) break;
 
         // plan one step per held pair (Fig. 1's Align: ls and ss, A6)
-        Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0};
+        Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0, 0u};
         int32_t vmax = 0, kstar = 0;
-        bool local = false;
+        bool local = false;                 // scanned by its own lane (wide matrices)
+        bool flat = false;                  // scanned as units of the flattened list
         if (busy) {
             const int32_t Lrem = L.nl - L.Lp, Srem = L.ns - L.Sp;
             const int32_t ls = max((int32_t)(((uint64_t)Lrem * L.lf) >> 16), 1);
@@ -183,18 +199,57 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             const int64_t ssw = (int64_t)(((uint64_t)Srem * L.sf * u) >> 32);
             g.ls = ls;
             g.ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
-            const int64_t iters = (int64_t)((ls - g.ss + 4) >> 2) * (g.ss + (L.qsmall ? 3 : 0));
-            local = iters <= kLocalIters;
-            if (local) {
-                lane_scan_t<P16>(L.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, g, sp.bias, sp.flush, vmax, kstar);
+            const int32_t nchunk = (ls - g.ss + 4) >> 2;
+            const int32_t niter = g.ss + (L.qsmall ? 3 : 0);
+            if constexpr (P16) {
+                flat = ls - g.ss < 65536 && (nchunk >= kFlatMinChunks || niter <= kFlatMaxIters);
+                if (!flat) plan_grid(g);
             } else {
-                plan_grid(g);
-                plans[lane] = g;
+                local = (int64_t)nchunk * niter <= kLocalIters;
+                if (local) lane_scan_t<P16>(L.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, g, sp.bias, sp.flush,
+                                            vmax, kstar);
+                else plan_grid(g);
             }
+        }
+        if constexpr (P16) {
+            // Flattened scan: the chunks of every flat step, in lane order,
+            // form one list of units dealt to the 32 lanes, 32 at a time.  A
+            // unit's lane finds its step from the first-unit indices in the
+            // plan slots and folds the chunk's best into the step's key.
+            const int units = flat ? (g.ls - g.ss + kUnitShifts) / kUnitShifts : 0;
+            int incl = units;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            g.u0 = incl - units;
+            plans[lane] = g;
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                const int u = base + lane;
+                if (u < total) {
+                    const int i = flat_owner(plans, u);
+                    const Plan h = plans[i];
+                    const int k0 = kUnitShifts * (u - h.u0);
+                    const uint32_t *pr = h.qsmall ? qc.prof_rev : qc.prof_fwd;
+                    const uint32_t key = kUnitShifts == 8 ? unit8_key(pr, R, sp.qlen, h, k0, h.ls - h.ss + 1, sp.flush)
+                                                          : unit_key(pr, R, sp.qlen, h, k0, h.ls - h.ss + 1, sp.flush);
+                    atomicMax(&plans[i].key, key);
+                }
+            }
+            __syncwarp();
+            if (flat) {
+                const uint32_t key = plans[lane].key;
+                vmax = (int32_t)(key >> 16) - sp.bias * g.ss;
+                kstar = (int32_t)(0xFFFFu - (key & 0xFFFFu));
+            }
+        } else {
+            if (busy && !local) plans[lane] = g;
         }
         __syncwarp();
         // the other steps, one pair at a time, by the whole warp
-        unsigned coop = __ballot_sync(0xFFFFFFFFu, busy && !local);
+        unsigned coop = __ballot_sync(0xFFFFFFFFu, busy && !local && !flat);
         while (coop) {
             const int i = __ffs(coop) - 1;
             coop &= coop - 1;
