@@ -144,7 +144,7 @@ struct PosQueue {
 
 template <bool P16>
 __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, const QueryCtx &qc,
-                                          const PosQueue &qu, Plan *plans, int lane)
+                                          const PosQueue &qu, Plan *plans, int32_t *ranks, int lane)
 {
     const int R = profile_stride(sp.qlen);
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -211,20 +211,39 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
                 else plan_grid(g);
             }
         }
+        int slot = lane;                    // this lane's plan slot
         if constexpr (P16) {
-            // Flattened scan: the chunks of every flat step, in lane order,
-            // form one list of units dealt to the 32 lanes, 32 at a time.  A
-            // unit's lane finds its step from the first-unit indices in the
-            // plan slots and folds the chunk's best into the step's key.
+            // Flattened scan: the chunks of every flat step form one list of
+            // units dealt to the 32 lanes, 32 at a time.  Steps are ranked by
+            // role and iterations per unit (a bitonic sort across the warp)
+            // so that the units sharing a pass have similar trip counts; plan
+            // slot r holds the step of rank r and its first unit index.  A
+            // unit's lane finds its step by binary search over the slots and
+            // folds the chunk's best into the step's key.
             const int units = flat ? (g.ls - g.ss + kUnitShifts) / kUnitShifts : 0;
-            int incl = units;
+            const uint32_t iters = (uint32_t)min(g.ss + 3 * g.qsmall, (1 << 24) - 1);
+            uint32_t sk = flat ? ((uint32_t)g.qsmall << 30) | (iters << 5) | (uint32_t)lane
+                               : 0x80000000u | (uint32_t)lane;
+            for (int k = 2; k <= 32; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, sk, j);
+                    const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+                    sk = take_min ? min(sk, o) : max(sk, o);
+                }
+            }
+            const int src = (int)(sk & 31u);        // the lane whose step has rank `lane`
+            const int ru = __shfl_sync(0xFFFFFFFFu, units, src);
+            int incl = ru;
             for (int o = 1; o < 32; o <<= 1) {
                 const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                 if (lane >= o) incl += x;
             }
             const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            g.u0 = incl - units;
-            plans[lane] = g;
+            ranks[src] = lane;
+            __syncwarp();
+            slot = ranks[lane];
+            g.u0 = __shfl_sync(0xFFFFFFFFu, incl - ru, slot);
+            plans[slot] = g;
             __syncwarp();
             for (int base = 0; base < total; base += 32) {
                 const int u = base + lane;
@@ -240,12 +259,13 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             }
             __syncwarp();
             if (flat) {
-                const uint32_t key = plans[lane].key;
+                const uint32_t key = plans[slot].key;
                 vmax = (int32_t)(key >> 16) - sp.bias * g.ss;
                 kstar = (int32_t)(0xFFFFu - (key & 0xFFFFu));
             }
         } else {
             if (busy && !local) plans[lane] = g;
+            ranks[lane] = lane;
         }
         __syncwarp();
         // the other steps, one pair at a time, by the whole warp
@@ -253,7 +273,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         while (coop) {
             const int i = __ffs(coop) - 1;
             coop &= coop - 1;
-            const Plan h = plans[i];
+            const Plan h = plans[ranks[i]];
             int32_t v, k;
             coop_scan_t<P16>(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
             if (lane == i) { vmax = v; kstar = k; }
@@ -294,6 +314,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ Plan plans[kWarpsPerCta][32];
+    __shared__ int32_t ranks[kWarpsPerCta][32];
     const uint32_t *prof = prof_g;
     if (kSmem) {
         const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
@@ -308,7 +329,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
     qc.scores = scores;
     qc.cells = cells_out;
     const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
-    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], ranks[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
 typedef void (*ScanKernelFn)(DbView, ScanQueue, const uint32_t *, SParams, int32_t *, int64_t *);
@@ -487,6 +508,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ Plan plans[kWarpsPerCta][32];
+    __shared__ int32_t ranks[kWarpsPerCta][32];
     __shared__ long long s_item;
     __shared__ unsigned s_pos;
     const uint32_t *prof_s = reinterpret_cast<const uint32_t *>(smem_raw);
@@ -535,7 +557,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
                     qc.prof_rev = prof_s;
                     qc.prof_fwd = prof_s;
                     const PosQueue pq = {r0, max(r0, min(bs.long_end, r1)), r1, &s_pos};
-                    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+                    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], ranks[threadIdx.x >> 5], threadIdx.x & 31);
                     __syncthreads();                        // all warps are done with s_pos
                 }
             } else {
@@ -543,7 +565,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
                 qc.prof_rev = pg;
                 qc.prof_fwd = pg + words;
                 const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
-                run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], threadIdx.x & 31);
+                run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], ranks[threadIdx.x >> 5], threadIdx.x & 31);
             }
         }
         __syncthreads();
