@@ -66,7 +66,7 @@ constexpr int kLocalIters = 64;
 #define HS_FLAT_MIN_CHUNKS 16
 #endif
 #ifndef HS_FLAT_MAX_ITERS
-#define HS_FLAT_MAX_ITERS 64
+#define HS_FLAT_MAX_ITERS 128
 #endif
 #ifndef HS_UNIT_SHIFTS
 #define HS_UNIT_SHIFTS 4
@@ -303,18 +303,28 @@ struct ScanQueue {
     int rev_off, fwd_off;           // word offsets of the two role profiles
 };
 
+// Plain scan CTA shape: warps per CTA and the CTAs per SM the register
+// budget is sized for.
+#ifndef HS_SCAN_WARPS
+#define HS_SCAN_WARPS 8
+#endif
+#ifndef HS_SCAN_MINB
+#define HS_SCAN_MINB 3
+#endif
+constexpr int kScanWarps = HS_SCAN_WARPS;
+
 // kSmem: the profiles are staged in shared memory (known to the compiler, so
 // every profile read is a shared load); otherwise they are read in place from
 // global memory (database-order schedule with a query too long for both
 // roles to fit).  P16: 16-bit chunk sums (SParams::pair16).
 template <bool kSmem, bool P16>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
+__global__ void __launch_bounds__(kScanWarps * 32, HS_SCAN_MINB)
 scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
             int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
     extern __shared__ uint4 smem_raw[];
-    __shared__ Plan plans[kWarpsPerCta][32];
-    __shared__ int32_t ranks[kWarpsPerCta][32];
+    __shared__ Plan plans[kScanWarps][32];
+    __shared__ int32_t ranks[kScanWarps][32];
     const uint32_t *prof = prof_g;
     if (kSmem) {
         const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
@@ -441,13 +451,12 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
                                       : pick_scan_kernel(staged, kp.s.pair16 != 0);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        const int threads = (kp.s.mode == HS_MODE_FULL ? kWarpsPerCta : kScanWarps) * 32;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerCta * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        {
-            kern<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores, d_cells);
-        }
+        kern<<<per_sm * num_sms, threads, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores, d_cells);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         nl++;
