@@ -279,8 +279,7 @@ struct __align__(16) Plan {
     int32_t Lp, Sp, ls, ss;
     int32_t qsmall;       // the query is the small sequence
     int32_t lgk, lgj;     // lane grid: 2^lgk chunks x 2^lgj segments
-    int32_t u0;           // flattened scan: index of the step's first unit
-    uint32_t key;         // flattened scan: best (sum, shift) key so far
+    int32_t pad;
 };
 
 // Lanes form a Gk x Gj grid: Gk chunks of 4 shifts side by side, each chunk's
@@ -368,126 +367,22 @@ __device__ __forceinline__ void lane_scan(const uint32_t *prof, int R, int qlen,
     else lane_scan_t<false>(prof, R, qlen, g, bias, flush, vmax, kstar);
 }
 
-// 8-shift units: shifts k0..k0+3 in accumulator A, k0+4..k0+7 in B.
-// Query small: target letter tl[p] meets reversed-query column sbase - p in
-// A's word and column sbase - p + 4 in B's (the same profile row, 4 words
-// on), so one letter load and one row address serve both; B's iterations are
-// A's delayed by 4, p in [0, ss + 7) overall, with A's byte masks at p in
-// [0, 3) and [ss, ss + 3) and B's at p in [4, 7) and [ss + 4, ss + 7).
-__device__ __forceinline__ void rev_unit8(const uint32_t *prof, int R, const uint8_t *tl, int sbase, int ss,
-                                          int flush, Acc<true> &A, Acc<true> &B)
-{
-    const uint32_t *pw = prof + sbase;
-    if (ss < 7 || flush < 7) {                      // short window or wide matrix: mask every iteration
-        uint32_t x = 0, y = 0;
-        int n = 0;
-        for (int p = 0; p < ss + 7; p++) {
-            const uint32_t *row = pw + (int)tl[p] * R - p;
-            const uint32_t ma = p < ss + 3 ? edge_mask(p, ss) : 0u;
-            const uint32_t mb = p >= 4 ? edge_mask(p - 4, ss) : 0u;
-            if (ma) x += row[0] & ma;
-            if (mb) y += row[4] & mb;
-            if (++n == flush) { A.add(x); B.add(y); x = 0; y = 0; n = 0; }
-        }
-        A.add(x);
-        B.add(y);
-        return;
-    }
-    {   // p in [0, 7): A's leading edge, then B's
-        const uint32_t *r0 = pw + (int)tl[0] * R, *r1 = pw + (int)tl[1] * R - 1, *r2 = pw + (int)tl[2] * R - 2;
-        const uint32_t *r3 = pw + (int)tl[3] * R - 3, *r4 = pw + (int)tl[4] * R - 4, *r5 = pw + (int)tl[5] * R - 5;
-        const uint32_t *r6 = pw + (int)tl[6] * R - 6;
-        A.add((r0[0] & 0x000000FFu) + (r1[0] & 0x0000FFFFu) + (r2[0] & 0x00FFFFFFu) + r3[0] + r4[0] + r5[0] + r6[0]);
-        B.add((r4[4] & 0x000000FFu) + (r5[4] & 0x0000FFFFu) + (r6[4] & 0x00FFFFFFu));
-    }
-    for (int c = 7; c < ss; c += flush) {           // both words whole
-        const int ce = min(ss, c + flush);
-        uint32_t x = 0, y = 0;
-        for (int p = c; p < ce; p++) {
-            const uint32_t *row = pw + (int)tl[p] * R - p;
-            x += row[0];
-            y += row[4];
-        }
-        A.add(x);
-        B.add(y);
-    }
-    {   // p in [ss, ss + 7): A's trailing edge, then B's
-        const int e = ss;
-        const uint32_t *r0 = pw + (int)tl[e] * R - e, *r1 = pw + (int)tl[e + 1] * R - (e + 1);
-        const uint32_t *r2 = pw + (int)tl[e + 2] * R - (e + 2), *r3 = pw + (int)tl[e + 3] * R - (e + 3);
-        const uint32_t *r4 = pw + (int)tl[e + 4] * R - (e + 4), *r5 = pw + (int)tl[e + 5] * R - (e + 5);
-        const uint32_t *r6 = pw + (int)tl[e + 6] * R - (e + 6);
-        A.add((r0[0] & 0xFFFFFF00u) + (r1[0] & 0xFFFF0000u) + (r2[0] & 0xFF000000u));
-        B.add(r0[4] + r1[4] + r2[4] + r3[4] + (r4[4] & 0xFFFFFF00u) + (r5[4] & 0xFFFF0000u) + (r6[4] & 0xFF000000u));
-    }
-}
-
-// Query large: small letter ts[j] meets stored query columns s0 + j (A) and
-// s0 + j + 4 (B) of one profile row; no edges.
-__device__ __forceinline__ void fwd_unit8(const uint32_t *prof, int R, const uint8_t *ts, int s0, int ss, int flush,
-                                          Acc<true> &A, Acc<true> &B)
-{
-    const uint32_t *pw = prof + s0;
-    for (int c = 0; c < ss; c += flush) {
-        const int ce = min(ss, c + flush);
-        uint32_t x = 0, y = 0;
-        for (int j = c; j < ce; j++) {
-            const uint32_t *row = pw + (int)ts[j] * R + j;
-            x += row[0];
-            y += row[4];
-        }
-        A.add(x);
-        B.add(y);
-    }
-}
-
-// Best shift of an 8-shift unit as a flattened-scan key (see unit_key).
-__device__ __forceinline__ uint32_t unit8_key(const uint32_t *prof, int R, int qlen, const Plan &g, int k0,
-                                              int nshift, int flush)
-{
-    Acc<true> A, B;
-    A.zero();
-    B.zero();
-    if (g.qsmall) rev_unit8(prof, R, g.t + g.Lp + k0, qlen + 3 - g.Sp, g.ss, flush, A, B);
-    else fwd_unit8(prof, R, g.t + g.Sp, g.Lp + k0 + 4, g.ss, flush, A, B);
-    const uint32_t c = 0xFFFFu - (uint32_t)k0;
-    const int nv = nshift - k0;                     // shifts of this unit inside the step, >= 1
-    uint32_t key = __byte_perm(A.p01, c, 0x1054);
-    if (nv > 1) key = max(key, __byte_perm(A.p01, c - 1u, 0x3254));
-    if (nv > 2) key = max(key, __byte_perm(A.p23, c - 2u, 0x1054));
-    if (nv > 3) key = max(key, __byte_perm(A.p23, c - 3u, 0x3254));
-    if (nv > 4) key = max(key, __byte_perm(B.p01, c - 4u, 0x1054));
-    if (nv > 5) key = max(key, __byte_perm(B.p01, c - 5u, 0x3254));
-    if (nv > 6) key = max(key, __byte_perm(B.p23, c - 6u, 0x1054));
-    if (nv > 7) key = max(key, __byte_perm(B.p23, c - 7u, 0x3254));
-    return key;
-}
-
-// The step owning unit u of the flattened list: the last of the 32 plan
-// slots whose first unit is <= u (first units are non-decreasing; a slot
-// with no units shares its first unit with the next one, so the last match
-// always has units).
-__device__ __forceinline__ int flat_owner(const Plan *plans, int u)
-{
-    int i = 0;
-    for (int st = 16; st; st >>= 1)
-        if (plans[i + st].u0 <= u) i += st;
-    return i;
-}
-
 // One unit of the flattened scan: chunk k0..k0+3 of a step with all its
 // iterations, in 16-bit pair sums.  Returns the chunk's best shift as the
 // key (biased sum << 16) | (0xFFFF - k): the unsigned maximum of keys is the
 // largest V with the lowest k among equals, as Fig. 1's strict '>' keeps.
 // Shifts at or past nshift are left out.  Needs biased sums < 65536 (the
-// 16-bit pair condition) and nshift <= 65536.
-__device__ __forceinline__ uint32_t unit_key(const uint32_t *prof, int R, int qlen, const Plan &g, int k0,
-                                             int nshift, int flush)
+// 16-bit pair condition) and nshift <= 65536.  The window is given by tb
+// (target letters: t + Lp when the query is small, t + Sp otherwise) and col
+// (stored column base: qlen + 3 - Sp, or Lp + 4), as a flat step's
+// descriptor holds them.
+__device__ __forceinline__ uint32_t unit_key_at(const uint32_t *prof, int R, const uint8_t *tb, int col, int ss,
+                                                bool qsmall, int k0, int nshift, int flush)
 {
     Acc<true> A;
     A.zero();
-    if (g.qsmall) rev_segment<true>(prof, R, g.t + g.Lp + k0, qlen + 3 - g.Sp, g.ss, 0, g.ss + 3, true, true, flush, A);
-    else fwd_chunk<true>(prof, R, g.t + g.Sp, g.Lp + k0 + 4, 0, g.ss, flush, A);
+    if (qsmall) rev_segment<true>(prof, R, tb + k0, col, ss, 0, ss + 3, true, true, flush, A);
+    else fwd_chunk<true>(prof, R, tb, col + k0, 0, ss, flush, A);
     const uint32_t c = 0xFFFFu - (uint32_t)k0;
     const int nv = nshift - k0;                     // shifts of this chunk inside the step, >= 1
     uint32_t key = __byte_perm(A.p01, c, 0x1054);   // sum of shift k0 above 0xFFFF - k0
@@ -495,6 +390,51 @@ __device__ __forceinline__ uint32_t unit_key(const uint32_t *prof, int R, int ql
     if (nv > 2) key = max(key, __byte_perm(A.p23, c - 2u, 0x1054));
     if (nv > 3) key = max(key, __byte_perm(A.p23, c - 3u, 0x3254));
     return key;
+}
+
+__device__ __forceinline__ uint32_t unit_key(const uint32_t *prof, int R, int qlen, const Plan &g, int k0,
+                                             int nshift, int flush)
+{
+    return g.qsmall ? unit_key_at(prof, R, g.t + g.Lp, qlen + 3 - g.Sp, g.ss, true, k0, nshift, flush)
+                    : unit_key_at(prof, R, g.t + g.Sp, g.Lp + 4, g.ss, false, k0, nshift, flush);
+}
+
+// A flat step as its units see it, 16 bytes: the target base (two words),
+// stored column base | ss << 16, and (nshift - 1) | qsmall << 16.  Column
+// base and ss are below 65536 because query lengths are; flat steps have
+// nshift <= 65536.
+__device__ __forceinline__ uint4 flat_desc(const Plan &g, int qlen)
+{
+    const uint8_t *tb = g.qsmall ? g.t + g.Lp : g.t + g.Sp;
+    const uint32_t col = g.qsmall ? (uint32_t)(qlen + 3 - g.Sp) : (uint32_t)(g.Lp + 4);
+    const uint64_t a = reinterpret_cast<uint64_t>(tb);
+    uint4 d;
+    d.x = (uint32_t)a;
+    d.y = (uint32_t)(a >> 32);
+    d.z = col | ((uint32_t)g.ss << 16);
+    d.w = (uint32_t)(g.ls - g.ss) | ((uint32_t)g.qsmall << 16);
+    return d;
+}
+
+__device__ __forceinline__ uint32_t desc_key(const uint32_t *prof_rev, const uint32_t *prof_fwd, int R,
+                                             const uint4 &d, int k0, int flush)
+{
+    const uint8_t *tb = reinterpret_cast<const uint8_t *>(((uint64_t)d.y << 32) | d.x);
+    const bool qsmall = (d.w >> 16) != 0;
+    return unit_key_at(qsmall ? prof_rev : prof_fwd, R, tb, (int)(d.z & 0xFFFFu), (int)(d.z >> 16), qsmall, k0,
+                       (int)(d.w & 0xFFFFu) + 1, flush);
+}
+
+// The step owning unit u of the flattened list: the last of the 32 rank
+// slots whose first unit is <= u (first units are non-decreasing; a slot
+// with no units shares its first unit with the next one, so the last match
+// always has units).
+__device__ __forceinline__ int flat_owner(const int32_t *u0, int u)
+{
+    int i = 0;
+    for (int st = 16; st; st >>= 1)
+        if (u0[i + st] <= u) i += st;
+    return i;
 }
 
 // ---------------------------------------------------------------------------

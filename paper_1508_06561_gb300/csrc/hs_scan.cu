@@ -68,11 +68,7 @@ constexpr int kLocalIters = 64;
 #ifndef HS_FLAT_MAX_ITERS
 #define HS_FLAT_MAX_ITERS 128
 #endif
-#ifndef HS_UNIT_SHIFTS
-#define HS_UNIT_SHIFTS 4
-#endif
 constexpr int kFlatMinChunks = HS_FLAT_MIN_CHUNKS;
-constexpr int kUnitShifts = HS_UNIT_SHIFTS;         // shifts per unit of the flattened list: 4 or 8
 constexpr int kFlatMaxIters = HS_FLAT_MAX_ITERS;
 
 struct QueryCtx {
@@ -136,6 +132,47 @@ __device__ __forceinline__ void lane_settle(Lane &L, const SParams &sp, const Qu
     }
 }
 
+// Per-warp shared slots of the flattened scan, in rank order: each flat
+// step's descriptor, first unit and best key, and each lane's rank.
+struct FlatSlots {
+    uint4 desc[32];
+    int32_t u0[32];
+    uint32_t key[32];
+    int32_t rank[32];
+};
+
+#ifndef HS_KEY_COMBINE
+#define HS_KEY_COMBINE 1
+#endif
+
+// Fold a pass's unit keys into their steps' keys.  Units of one step sit in
+// adjacent lanes (owner -1: no unit).
+__device__ __forceinline__ void fold_keys(FlatSlots *fs, int i, uint32_t key, int lane)
+{
+#if HS_KEY_COMBINE == 0
+    if (i >= 0) atomicMax(&fs->key[i], key);
+#elif HS_KEY_COMBINE == 1
+    // a pass of one step (the common case after ranking): one warp maximum
+    const int i0 = __shfl_sync(0xFFFFFFFFu, i, 0);
+    if (__all_sync(0xFFFFFFFFu, i == i0)) {
+        const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, key);
+        if (lane == 0) atomicMax(&fs->key[i0], m);
+    } else if (i >= 0) {
+        atomicMax(&fs->key[i], key);
+    }
+#else
+    // segmented maximum over runs of equal owners, one update per run
+    uint32_t k = key;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t ok = __shfl_down_sync(0xFFFFFFFFu, k, d);
+        const int oi = __shfl_down_sync(0xFFFFFFFFu, i, d);
+        if (lane + d < 32 && oi == i) k = max(k, ok);
+    }
+    const int pi = __shfl_up_sync(0xFFFFFFFFu, i, 1);
+    if (i >= 0 && (lane == 0 || pi != i)) atomicMax(&fs->key[i], k);
+#endif
+}
+
 // Queue positions [begin, end) of the length order; [begin, long_end) long.
 struct PosQueue {
     int64_t begin, long_end, end;
@@ -144,7 +181,7 @@ struct PosQueue {
 
 template <bool P16>
 __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, const QueryCtx &qc,
-                                          const PosQueue &qu, Plan *plans, int32_t *ranks, int lane)
+                                          const PosQueue &qu, Plan *plans, FlatSlots *fs, int lane)
 {
     const int R = profile_stride(sp.qlen);
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -188,7 +225,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         if (!open && __ballot_sync(0xFFFFFFFFu, busy) == 0) break;
 
         // plan one step per held pair (Fig. 1's Align: ls and ss, A6)
-        Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0, 0u};
+        Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0};
         int32_t vmax = 0, kstar = 0;
         bool local = false;                 // scanned by its own lane (wide matrices)
         bool flat = false;                  // scanned as units of the flattened list
@@ -211,16 +248,16 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
                 else plan_grid(g);
             }
         }
-        int slot = lane;                    // this lane's plan slot
         if constexpr (P16) {
             // Flattened scan: the chunks of every flat step form one list of
             // units dealt to the 32 lanes, 32 at a time.  Steps are ranked by
             // role and iterations per unit (a bitonic sort across the warp)
-            // so that the units sharing a pass have similar trip counts; plan
-            // slot r holds the step of rank r and its first unit index.  A
-            // unit's lane finds its step by binary search over the slots and
-            // folds the chunk's best into the step's key.
-            const int units = flat ? (g.ls - g.ss + kUnitShifts) / kUnitShifts : 0;
+            // so that the units sharing a pass have similar trip counts; flat
+            // slot r holds the descriptor, first unit and key of the step of
+            // rank r.  A unit's lane finds its step by binary search over the
+            // first units and scores its chunk; the pass folds the chunk keys
+            // into the steps' keys.
+            const int units = flat ? (g.ls - g.ss + 4) >> 2 : 0;
             const uint32_t iters = (uint32_t)min(g.ss + 3 * g.qsmall, (1 << 24) - 1);
             uint32_t sk = flat ? ((uint32_t)g.qsmall << 30) | (iters << 5) | (uint32_t)lane
                                : 0x80000000u | (uint32_t)lane;
@@ -239,33 +276,33 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
                 if (lane >= o) incl += x;
             }
             const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            ranks[src] = lane;
+            fs->rank[src] = lane;
+            fs->u0[lane] = incl - ru;
+            fs->key[lane] = 0u;
             __syncwarp();
-            slot = ranks[lane];
-            g.u0 = __shfl_sync(0xFFFFFFFFu, incl - ru, slot);
-            plans[slot] = g;
+            const int slot = fs->rank[lane];
+            if (flat) fs->desc[slot] = flat_desc(g, sp.qlen);
+            else if (busy) plans[lane] = g;
             __syncwarp();
             for (int base = 0; base < total; base += 32) {
                 const int u = base + lane;
+                int i = -1;
+                uint32_t key = 0u;
                 if (u < total) {
-                    const int i = flat_owner(plans, u);
-                    const Plan h = plans[i];
-                    const int k0 = kUnitShifts * (u - h.u0);
-                    const uint32_t *pr = h.qsmall ? qc.prof_rev : qc.prof_fwd;
-                    const uint32_t key = kUnitShifts == 8 ? unit8_key(pr, R, sp.qlen, h, k0, h.ls - h.ss + 1, sp.flush)
-                                                          : unit_key(pr, R, sp.qlen, h, k0, h.ls - h.ss + 1, sp.flush);
-                    atomicMax(&plans[i].key, key);
+                    i = flat_owner(fs->u0, u);
+                    const uint4 d = fs->desc[i];
+                    key = desc_key(qc.prof_rev, qc.prof_fwd, R, d, 4 * (u - fs->u0[i]), sp.flush);
                 }
+                fold_keys(fs, i, key, lane);
             }
             __syncwarp();
             if (flat) {
-                const uint32_t key = plans[slot].key;
+                const uint32_t key = fs->key[slot];
                 vmax = (int32_t)(key >> 16) - sp.bias * g.ss;
                 kstar = (int32_t)(0xFFFFu - (key & 0xFFFFu));
             }
         } else {
             if (busy && !local) plans[lane] = g;
-            ranks[lane] = lane;
         }
         __syncwarp();
         // the other steps, one pair at a time, by the whole warp
@@ -273,7 +310,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         while (coop) {
             const int i = __ffs(coop) - 1;
             coop &= coop - 1;
-            const Plan h = plans[ranks[i]];
+            const Plan h = plans[i];
             int32_t v, k;
             coop_scan_t<P16>(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
             if (lane == i) { vmax = v; kstar = k; }
@@ -324,7 +361,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ Plan plans[kScanWarps][32];
-    __shared__ int32_t ranks[kScanWarps][32];
+    __shared__ FlatSlots flat_slots[kScanWarps];
     const uint32_t *prof = prof_g;
     if (kSmem) {
         const int64_t n16 = qu.smem_words / 4;          // profile words are a multiple of 4
@@ -339,7 +376,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
     qc.scores = scores;
     qc.cells = cells_out;
     const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
-    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], ranks[threadIdx.x >> 5], threadIdx.x & 31);
+    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
 typedef void (*ScanKernelFn)(DbView, ScanQueue, const uint32_t *, SParams, int32_t *, int64_t *);
@@ -517,7 +554,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ Plan plans[kWarpsPerCta][32];
-    __shared__ int32_t ranks[kWarpsPerCta][32];
+    __shared__ FlatSlots flat_slots[kWarpsPerCta];
     __shared__ long long s_item;
     __shared__ unsigned s_pos;
     const uint32_t *prof_s = reinterpret_cast<const uint32_t *>(smem_raw);
@@ -566,7 +603,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
                     qc.prof_rev = prof_s;
                     qc.prof_fwd = prof_s;
                     const PosQueue pq = {r0, max(r0, min(bs.long_end, r1)), r1, &s_pos};
-                    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], ranks[threadIdx.x >> 5], threadIdx.x & 31);
+                    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
                     __syncthreads();                        // all warps are done with s_pos
                 }
             } else {
@@ -574,7 +611,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
                 qc.prof_rev = pg;
                 qc.prof_fwd = pg + words;
                 const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
-                run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], ranks[threadIdx.x >> 5], threadIdx.x & 31);
+                run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
             }
         }
         __syncthreads();

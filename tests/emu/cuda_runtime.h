@@ -11,6 +11,7 @@
 #define __forceinline__ inline
 #define __align__(x) alignas(x)
 typedef int cudaError_t;
+struct uint4 { unsigned x, y, z, w; };
 typedef void *cudaStream_t;
 typedef void *cudaEvent_t;
 template <class T> inline T __ldg(const T *p) { return *p; }

@@ -5,7 +5,8 @@
 // entries, and every profile/target read must stay inside its buffer: the
 // buffers end at PROT_NONE guard pages, so a stray read faults.
 // Also checked: the flattened scan's per-chunk keys (their maximum over a
-// step's chunks gives the step's best shift) and its owner search.
+// step's chunks gives the step's best shift), the same keys through a flat
+// step's packed descriptor, and the owner search.
 // Both accumulator forms are checked: 32-bit sums always, 16-bit pair sums
 // whenever range * (qlen + 3) <= 65535 (the condition the library uses).
 // usage: lane_emu SEED [MIN MAX]   (matrix entries drawn from [MIN, MAX])
@@ -105,9 +106,12 @@ int main(int argc, char **argv) {
                     if ((int)(key >> 16) - bias * ss != bestv || (int)(0xFFFFu - (key & 0xFFFFu)) != bestk) {
                         printf("unit_key mismatch trial %d\n", trial); return 1;
                     }
-                    uint32_t key8 = 0;
-                    for (int k0 = 0; k0 < nshift; k0 += 8) key8 = std::max(key8, unit8_key(prof, R, qlen, g, k0, nshift, flush));
-                    if (key8 != key) { printf("unit8_key mismatch trial %d\n", trial); return 1; }
+                    // the same through a flat step's descriptor
+                    const uint4 dsc = flat_desc(g, qlen);
+                    for (int k0 = 0; k0 < nshift; k0 += 4)
+                        if (desc_key(prof, prof, R, dsc, k0, flush) != unit_key(prof, R, qlen, g, k0, nshift, flush)) {
+                            printf("desc_key mismatch trial %d\n", trial); return 1;
+                        }
                 }
                 int niter = qsmall ? ss + 3 : ss;
                 for (int k0 = 0; k0 < nshift; k0 += 4) {
@@ -124,16 +128,16 @@ int main(int argc, char **argv) {
     }
     // owner search of the flattened list: random unit counts (many zero)
     for (int trial = 0; trial < 20000; trial++) {
-        Plan plans[32];
+        int32_t firsts[32];
         int u0 = 0, owner[32 * 64];
         for (int j = 0; j < 32; j++) {
             int n = rng() % 3 == 0 ? 0 : (int)(rng() % 64);
-            plans[j].u0 = u0;
+            firsts[j] = u0;
             for (int x = 0; x < n; x++) owner[u0 + x] = j;
             u0 += n;
         }
         for (int u = 0; u < u0; u++)
-            if (flat_owner(plans, u) != owner[u]) { printf("owner mismatch trial %d unit %d\n", trial, u); return 1; }
+            if (flat_owner(firsts, u) != owner[u]) { printf("owner mismatch trial %d unit %d\n", trial, u); return 1; }
     }
     printf("emu ok: %ld shift sums checked\n", checks);
     return 0;
