@@ -57,7 +57,7 @@ struct Workspace {
     uint32_t *prof;                     // [2 * profile words] reversed, then forward query profile
     int32_t *scores;                    // [n] by database index
     uint32_t *counters;                 // [kNumCounters], zeroed per search
-    uint64_t *cand;                     // [topk_ctas * k] per-CTA top-k keys
+    uint64_t *cand;                     // [topk_ctas * k] per-CTA top-k keys, then [topk_ctas] k-th keys
     int64_t *hit_idx;                   // [k] database index of each ranked hit
     int32_t *hit_score;                 // [k]
     uint32_t *slots;                    // [k * slot_stride] replayed ops
@@ -83,7 +83,7 @@ struct BatchLayout {
     int32_t *scores;                    // [nq][n]
     unsigned *counters;                 // item counter, replay ticket, then one top-k ticket per query
     unsigned *item_ctr, *replay_ticket, *topk_tickets;
-    uint64_t *cand;                     // [nq][kTopkCtas * k]
+    uint64_t *cand;                     // [nq][kTopkCtas * (k + 1)]
     int64_t *hit_idx;                   // [nq * k]
     int32_t *hit_score;                 // [nq * k]
     uint32_t *slots;                    // [nq * k][slot_stride]

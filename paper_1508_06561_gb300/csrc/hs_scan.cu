@@ -740,6 +740,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
         int32_t best, again;
         if (ra.hit_score && ra.hit_score[slot] < sp.min_score) {
             best = again = ra.hit_score[slot];      // below the reporting threshold: no alignment
+        } else if (ra.hit_score && sp.rounds == 1) {
+            // one round: it is the best one, and the scan's score checks the replay
+            best = ra.hit_score[slot];
+            again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span)
+                                            : align_round<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span);
         } else {
             best = align_pair(c, sp, (uint64_t)d, lane, cells, &br);
             again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span)

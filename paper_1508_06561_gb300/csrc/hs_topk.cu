@@ -3,9 +3,14 @@
 // ascending.  Each pair becomes the 64-bit key
 //     ((score ^ 0x80000000) << 32) | (0xFFFFFFFF - index)
 // so a larger key is a better hit and all keys are distinct.  Every CTA
-// selects the k largest keys of its slice with an MSB-first radix select in
-// shared memory; the last CTA to finish selects the k largest of those
-// candidates, sorts them and writes the ranked (index, score) list.
+// selects the k largest keys of its slice and publishes them with its k-th
+// key: the threshold score comes from 12-bit digit histograms of the score
+// above the slice minimum (one pass when the slice's scores span less than
+// 4096 values), ties at the threshold go to the lowest indices.  The global k-th key
+// is at least every full slice's k-th key, so the last CTA to finish keeps
+// only the candidates at or above the largest of those (one pass; at least
+// k of them), sorts them in shared memory and writes the ranked (index,
+// score) list; if they do not fit, it radix-selects over all candidates.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -19,21 +24,13 @@ namespace {
 
 constexpr int kSortMax = HS_MAX_K;     // bitonic sort buffer (keys)
 
-struct ScoreKeys {      // the slice [lo, lo+m) of the score array
-    const int32_t *scores;
-    int64_t lo;
-    __device__ __forceinline__ uint64_t operator()(int64_t i) const
-    {
-        const uint32_t s = (uint32_t)((volatile const int32_t *)scores)[lo + i] ^ 0x80000000u;
-        return ((uint64_t)s << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)(lo + i));
-    }
-};
-
 struct CandKeys {       // candidates written by the other CTAs (0 = empty slot)
     const uint64_t *cand;
     __device__ __forceinline__ uint64_t operator()(int64_t i) const
     {
-        return ((volatile const uint64_t *)cand)[i];
+        // from L2 (their writes are fenced before the ticket), not volatile,
+        // so the loads of a pass overlap
+        return __ldcg(cand + i);
     }
 };
 
@@ -108,17 +105,146 @@ __device__ void gather_at_least(const Keys &key, int64_t m, uint64_t kth, uint64
     __syncthreads();
 }
 
-// Batched: blockIdx.y is the query; its scores, candidates, hits and ticket
-// sit at y * n, y * (gridDim.x * k), y * hit_stride and y.
+// Bitonic sort of buf[0, pow2), descending (pow2 a power of two).
+__device__ void sort_desc(uint64_t *buf, int pow2)
+{
+    for (int size = 2; size <= pow2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool desc = (i & size) == 0;
+                    const uint64_t a = buf[i], b = buf[j];
+                    if (desc ? (a < b) : (a > b)) { buf[i] = b; buf[j] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+constexpr int kDigitBits = 12;
+constexpr int kBins = 1 << kDigitBits;
+constexpr int kBinsPerThread = kBins / kTopkThreads;
+static_assert(kBins % kTopkThreads == 0, "histogram bins split evenly over the threads");
+
+struct SliceSmem {
+    uint32_t umin, umax;
+    uint32_t wsum[kTopkThreads / 32];
+    uint32_t bin, above;
+    uint32_t count, ties;
+    uint64_t kth;
+};
+
+// The kk largest keys of the slice [lo, lo + m) of the scores into out[0,
+// kk) (any order); returns the smallest of them.  u = score ^ 0x80000000 is
+// the score in key order.  Needs blockDim.x == kTopkThreads.
+__device__ uint64_t slice_select(const int32_t *scores, int64_t lo, int64_t m, uint32_t kk, uint64_t *out,
+                                 uint32_t *hist, SliceSmem &ss)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nw = kTopkThreads / 32;
+    // 1. the slice's range of u
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const uint32_t u = (uint32_t)__ldg(scores + lo + i) ^ 0x80000000u;
+        mn = min(mn, u);
+        mx = max(mx, u);
+    }
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if (threadIdx.x == 0) { ss.umin = 0xFFFFFFFFu; ss.umax = 0u; ss.count = 0u; ss.ties = 0u; ss.kth = 0ull; }
+    __syncthreads();
+    if (lane == 0) { atomicMin(&ss.umin, mn); atomicMax(&ss.umax, mx); }
+    __syncthreads();
+    const uint32_t umin = ss.umin, range = ss.umax - umin;
+    // 2. the k-th key's score: digits of d = u - umin, most significant first
+    const int bits = range ? 32 - __clz(range) : 0;
+    int shift = bits > 0 ? ((bits - 1) / kDigitBits) * kDigitBits : 0;
+    uint32_t prefix = 0u, remaining = kk;
+    for (;;) {
+        for (int b = threadIdx.x; b < kBins; b += blockDim.x) hist[b] = 0u;
+        __syncthreads();
+        const uint64_t hi_mask = ~0ull << (shift + kDigitBits);     // digits already fixed
+        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+            const uint32_t d = ((uint32_t)__ldg(scores + lo + i) ^ 0x80000000u) - umin;
+            if ((((uint64_t)(d ^ prefix)) & hi_mask) == 0) atomicAdd(&hist[(d >> shift) & (kBins - 1)], 1u);
+        }
+        __syncthreads();
+        // keys in bins above each thread's bins: suffix sums over threads
+        const int b0 = threadIdx.x * kBinsPerThread;
+        uint32_t tot = 0u;
+#pragma unroll
+        for (int j = 0; j < kBinsPerThread; j++) tot += hist[b0 + j];
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_down_sync(0xFFFFFFFFu, incl, o);
+            if (lane + o < 32) incl += y;
+        }
+        if (lane == 0) ss.wsum[warp] = incl;
+        __syncthreads();
+        uint32_t run = incl - tot;
+        for (int w = warp + 1; w < nw; w++) run += ss.wsum[w];
+        for (int j = kBinsPerThread - 1; j >= 0; j--) {
+            const uint32_t c = hist[b0 + j];
+            if (run < remaining && run + c >= remaining) { ss.bin = (uint32_t)(b0 + j); ss.above = run; }
+            run += c;
+        }
+        __syncthreads();
+        prefix |= ss.bin << shift;
+        remaining -= ss.above;
+        __syncthreads();                            // ss.bin is read before the next pass sets it
+        if (shift == 0) break;
+        shift -= kDigitBits;
+    }
+    const uint32_t thr = umin + prefix;             // the k-th key's u; `remaining` keys at it are taken
+    // 3. every key above thr, and the first `remaining` at thr in index order
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int64_t base = 0; base < m; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t u = i < m ? (uint32_t)__ldg(scores + lo + i) ^ 0x80000000u : 0u;
+        const bool tie = i < m && u == thr, above = i < m && u > thr;
+        const unsigned tb = __ballot_sync(0xFFFFFFFFu, tie);
+        if (lane == 0) ss.wsum[warp] = (uint32_t)__popc(tb);
+        __syncthreads();
+        uint32_t rank = ss.ties + (uint32_t)__popc(tb & lt_mask);
+        for (int w = 0; w < warp; w++) rank += ss.wsum[w];
+        const bool take = above || (tie && rank < remaining);
+        if (take) {
+            const uint64_t key = ((uint64_t)u << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)(lo + i));
+            out[atomicAdd(&ss.count, 1u)] = key;
+            if (tie && rank == remaining - 1u) ss.kth = key;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0u;
+            for (int w = 0; w < nw; w++) t += ss.wsum[w];
+            ss.ties += t;
+        }
+        __syncthreads();
+    }
+    return ss.kth;
+}
+
+// Batched: blockIdx.y is the query; its scores, candidates (gridDim.x * k
+// keys, then gridDim.x k-th keys), hits and ticket sit at y * n,
+// y * gridDim.x * (k + 1), y * hit_stride and y.
 __global__ void __launch_bounds__(kTopkThreads)
 topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t *hit_idx,
             int32_t *hit_score, uint32_t *ticket, int32_t hit_stride)
 {
     __shared__ SelectSmem sm;
-    __shared__ uint64_t sortbuf[kSortMax];
+    __shared__ SliceSmem ss;
+    __shared__ union {
+        uint64_t sortbuf[kSortMax];         // phase 2
+        uint32_t hist[kBins];               // phase 1
+    } buf;
+    uint64_t *sortbuf = buf.sortbuf;
     __shared__ int is_last;
     scores += (int64_t)blockIdx.y * n;
-    cand += (int64_t)blockIdx.y * gridDim.x * k;
+    cand += (int64_t)blockIdx.y * gridDim.x * (k + 1);
+    uint64_t *kths = cand + (int64_t)gridDim.x * k;
     hit_idx += (int64_t)blockIdx.y * hit_stride;
     hit_score += (int64_t)blockIdx.y * hit_stride;
     ticket += blockIdx.y;
@@ -130,12 +256,13 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
     uint64_t *mine = cand + (int64_t)blockIdx.x * k;
     for (int i = threadIdx.x; i < k; i += blockDim.x) mine[i] = 0;
     __syncthreads();
+    uint64_t bound = 0;                     // a lower bound of the global k-th key (0: none)
     if (m > 0) {
-        ScoreKeys keys{scores, lo};
         const uint32_t kk = (uint32_t)min((int64_t)k, m);
-        const uint64_t kth = radix_kth(keys, m, kk, sm);
-        gather_at_least(keys, m, kth, mine, sm);
+        const uint64_t kth = slice_select(scores, lo, m, kk, mine, buf.hist, ss);
+        if (m >= k) bound = kth;
     }
+    if (threadIdx.x == 0) kths[blockIdx.x] = bound;
 
     __threadfence();
     __syncthreads();
@@ -147,27 +274,36 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
     // phase 2: the k best of all candidates, sorted
     const int64_t mc = (int64_t)gridDim.x * k;
     const uint32_t kk = (uint32_t)min((int64_t)k, n);
-    CandKeys ck{cand};
-    const uint64_t kth = radix_kth(ck, mc, kk, sm);
-    int pow2 = 1;
-    while (pow2 < (int)kk) pow2 <<= 1;
-    for (int i = threadIdx.x; i < pow2; i += blockDim.x) sortbuf[i] = 0;
+    if (threadIdx.x == 0) { sm.prefix = 0; sm.count = 0; }
     __syncthreads();
-    gather_at_least(ck, mc, kth, sortbuf, sm);
-    // bitonic sort, descending
-    for (int size = 2; size <= pow2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool desc = (i & size) == 0;
-                    const uint64_t a = sortbuf[i], b = sortbuf[j];
-                    if (desc ? (a < b) : (a > b)) { sortbuf[i] = b; sortbuf[j] = a; }
-                }
-            }
-            __syncthreads();
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
+        atomicMax(reinterpret_cast<unsigned long long *>(&sm.prefix), (unsigned long long)__ldcg(kths + c));
+    __syncthreads();
+    const uint64_t floor_key = sm.prefix;   // the largest slice k-th key
+    for (int64_t i = threadIdx.x; i < mc; i += blockDim.x) {
+        const uint64_t x = __ldcg(cand + i);
+        if (x != 0 && x >= floor_key) {
+            const uint32_t at = atomicAdd(&sm.count, 1u);
+            if (at < (uint32_t)kSortMax) sortbuf[at] = x;
         }
     }
+    __syncthreads();
+    const uint32_t kept = sm.count;
+    int pow2 = 1;
+    if (kept <= (uint32_t)kSortMax) {
+        while (pow2 < (int)kept) pow2 <<= 1;
+        for (int i = (int)kept + threadIdx.x; i < pow2; i += blockDim.x) sortbuf[i] = 0;
+        __syncthreads();
+    } else {
+        // more than fit: select the k-th key over all candidates, keep k
+        CandKeys ck{cand};
+        const uint64_t kth = radix_kth(ck, mc, kk, sm);
+        while (pow2 < (int)kk) pow2 <<= 1;
+        for (int i = threadIdx.x; i < pow2; i += blockDim.x) sortbuf[i] = 0;
+        __syncthreads();
+        gather_at_least(ck, mc, kth, sortbuf, sm);
+    }
+    sort_desc(sortbuf, pow2);
     for (int i = threadIdx.x; i < (int)kk; i += blockDim.x) {
         const uint64_t x = sortbuf[i];
         hit_idx[i] = (int64_t)(0xFFFFFFFFu - (uint32_t)(x & 0xFFFFFFFFu));
