@@ -477,14 +477,14 @@ def run_ours(args, world, rank, local):
     # Roofline of the scan kernel, T_roof = max(B / HBM, Ops / P_int): Ops = one
     # integer add per cell (the per-shift compare, about 1/ss of that, is left
     # out, so `achieved` errs low); P_int = SMs x 128 INT32 lanes x max SM
-    # clock; B = the residues, and per pair its schedule entry and two offsets
-    # read and its score written (28 B).
+    # clock; B = the residues, and per pair its schedule entry (4 B) and two
+    # offsets (16 B) read and its score (4 B) written.
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     scan_s = float(np.mean(scan_ms)) / 1000.0
     achieved = cells_per_search / scan_s / 1e12
     peak = sms * 128 * 2070e6 / 1e12
-    alg_bytes = db.residues + 28 * db.n
+    alg_bytes = db.residues + 24 * db.n
     hbm_gbs = measured_hbm_gbs()
     t_alu_us = cells_per_search / (peak * 1e12) * 1e6
     t_hbm_us = alg_bytes / (hbm_gbs * 1e9) * 1e6
