@@ -375,7 +375,10 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    P.build.build()
+    if rank == 0:
+        P.build.build()                     # no-op when the library is current
+    if world > 1:
+        torch.distributed.barrier()         # the other ranks load what rank 0 checked
     L = _lib.lib()
 
     db, q, k, cfg = workload(args.workload, rank)

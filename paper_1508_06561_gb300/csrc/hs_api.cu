@@ -551,8 +551,9 @@ static size_t batch_layout(int64_t n, int32_t nq, int64_t total_qlen, int32_t ma
     };
     const size_t kk = (size_t)std::max(k, 1), qq = (size_t)std::max(nq, 1);
     BatchLayout b = {};
-    b.counter_bytes = (int64_t)(sizeof(unsigned) * (2 + qq));
+    b.counter_bytes = (int64_t)(sizeof(unsigned) * (5 + qq));
     b.counters = reinterpret_cast<unsigned *>(take((size_t)b.counter_bytes));
+    b.qlist = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * 2 * qq));
     b.prof_off = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * qq));
     b.prof = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 2 * kNSym * (size_t)(total_qlen + 17 * qq)));
     b.bounds = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (kMaxChunks + 1)));
@@ -564,9 +565,10 @@ static size_t batch_layout(int64_t n, int32_t nq, int64_t total_qlen, int32_t ma
     b.slots = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * qq * kk * (size_t)b.slot_stride));
     b.slot_len = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * qq * kk));
     if (b.counters) {
-        b.item_ctr = b.counters;
-        b.replay_ticket = b.counters + 1;
-        b.topk_tickets = b.counters + 2;
+        b.item_ctrs = b.counters;
+        b.class_counts = b.counters + 2;
+        b.replay_ticket = b.counters + 4;
+        b.topk_tickets = b.counters + 5;
     }
     b.nq = nq;
     b.max_qlen = max_qlen;

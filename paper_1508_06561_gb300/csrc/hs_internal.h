@@ -81,8 +81,10 @@ struct BatchLayout {
     uint32_t *prof;                     // profiles of every query
     int64_t *bounds;                    // [nchunk + 1] chunk boundaries in the length order
     int32_t *scores;                    // [nq][n]
-    unsigned *counters;                 // item counter, replay ticket, then one top-k ticket per query
-    unsigned *item_ctr, *replay_ticket, *topk_tickets;
+    unsigned *counters;                 // item counters and query counts of the two length classes,
+                                        // replay ticket, then one top-k ticket per query
+    unsigned *item_ctrs, *class_counts, *replay_ticket, *topk_tickets;
+    int32_t *qlist;                     // [2][nq] queries of each length class
     uint64_t *cand;                     // [nq][kTopkCtas * (k + 1)]
     int64_t *hit_idx;                   // [nq * k]
     int32_t *hit_score;                 // [nq * k]
@@ -92,6 +94,7 @@ struct BatchLayout {
     int64_t counter_bytes;
 };
 constexpr int kMaxChunks = 8192;
+constexpr int kBatchShortLen = 512;     // batched scan: queries up to this long form the short class
 constexpr int kDefaultChunks = 1024;
 
 size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k);

@@ -532,8 +532,12 @@ __global__ void chunk_bounds_kernel(const int64_t *cumres, int64_t n, int32_t nc
     bounds[c] = c == nchunk ? n : lo;
 }
 
+// Queries of one length class (their profiles share one shared-memory size)
+// are listed by batch_classes_kernel; a scan launch covers one class.
 struct BatchScan {
     int32_t nq, nchunk;
+    const int32_t *qlist;           // the class's queries (batch indices)
+    const unsigned *qcount;         // how many
     const int64_t *qoffsets;        // [nq + 1]
     const uint64_t *seeds;          // [nq]
     const int64_t *prof_off;        // [nq] word offsets into prof
@@ -548,8 +552,11 @@ struct BatchScan {
 // as two sub-ranges, each with its role's profile staged, so every profile
 // read is a shared load.  Otherwise (database order, roles mixed) both role
 // profiles are read from global memory.
+#ifndef HS_BATCH_MINB
+#define HS_BATCH_MINB 3
+#endif
 template <bool kSmem, bool P16>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 2)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, HS_BATCH_MINB)
 scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
 {
     extern __shared__ uint4 smem_raw[];
@@ -559,7 +566,7 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
     __shared__ unsigned s_pos;
     const uint32_t *prof_s = reinterpret_cast<const uint32_t *>(smem_raw);
     int cur_q = -1, cur_role = -1;
-    const long long nitems = (long long)bs.nq * bs.nchunk;
+    const long long nitems = (long long)*bs.qcount * bs.nchunk;
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = (long long)atomicAdd(bs.item_ctr, 1u);
@@ -568,7 +575,8 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
         __syncthreads();
         const long long item = s_item;
         if (item >= nitems) break;
-        const int q = (int)(item / bs.nchunk), c = (int)(item - (long long)q * bs.nchunk);
+        const int ql = (int)(item / bs.nchunk), c = (int)(item - (long long)ql * bs.nchunk);
+        const int q = bs.qlist[ql];
         const int64_t b0 = bs.bounds[c], b1 = bs.bounds[c + 1];
         if (b0 < b1) {
             SParams sp = sp0;
@@ -626,6 +634,16 @@ static BatchKernelFn pick_batch_kernel(bool smem, bool p16)
     return p16 ? scan_batch_kernel<false, true> : scan_batch_kernel<false, false>;
 }
 
+// Splits the batch's queries into the length classes (qlen <= kBatchShortLen,
+// and longer), in any order within a class.
+__global__ void batch_classes_kernel(const int64_t *qoffsets, int32_t nq, int32_t *qlist, unsigned *counts)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int c = qoffsets[q + 1] - qoffsets[q] <= kBatchShortLen ? 0 : 1;
+        qlist[c * nq + atomicAdd(&counts[c], 1u)] = q;
+    }
+}
+
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
                               const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
                               cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order)
@@ -635,6 +653,9 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     chunk_bounds_kernel<<<(nchunk + 1 + 255) / 256, 256, 0, st>>>(d_cumres, db.n, nchunk, bl.bounds);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_classes_kernel<<<1, 256, 0, st>>>(bl.qoffsets, bl.nq, bl.qlist, bl.class_counts);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     BatchScan bs;
@@ -647,28 +668,38 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
     bs.bounds = bl.bounds;
     bs.long_end = long_end;
     bs.scores = bl.scores;
-    bs.item_ctr = bl.item_ctr;
     const BatchKernelFn kern = pick_batch_kernel(!input_order, kp.s.pair16 != 0);
-    const size_t smem = input_order ? 0 : (size_t)profile_words(bl.max_qlen) * 4;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerCta * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
     if (trace && trace->start) {
         e = cudaEventRecord(trace->start, st);
         if (e != cudaSuccess) return e;
     }
-    kern<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, bs, kp.s);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    // one launch per length class, its shared memory sized for the class
+    // (a class above the batch's longest query is known empty)
+    int nl = 3;
+    for (int c = 0; c < 2; c++) {
+        if (c == 1 && bl.max_qlen <= kBatchShortLen) break;
+        const int cls_len = c == 0 ? min(bl.max_qlen, kBatchShortLen) : bl.max_qlen;
+        bs.qlist = bl.qlist + (int64_t)c * bl.nq;
+        bs.qcount = bl.class_counts + c;
+        bs.item_ctr = bl.item_ctrs + c;
+        const size_t smem = input_order ? 0 : (size_t)profile_words(cls_len) * 4;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerCta * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
+        kern<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, bs, kp.s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        nl++;
+    }
     if (trace && trace->stop) {
         e = cudaEventRecord(trace->stop, st);
         if (e != cudaSuccess) return e;
     }
-    if (launches) *launches += 3;
+    if (launches) *launches += nl;
     return cudaSuccess;
 }
 

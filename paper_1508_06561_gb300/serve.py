@@ -8,7 +8,9 @@ the batch's device memory need (hs_search_batch_workspace_size and the
 query/ops buffers) fits the slot's budget and the batch has at most
 `max_batch` queries, then launches the batched search on that slot's stream.
 Requests that arrive while other batches run are admitted as soon as a slot
-and its memory free up, and several batches overlap on the device.  Results
+and its memory free up, and several batches overlap on the device.  A batch
+of one query (the common case at low load) runs the plain search entry point
+on the slot's buffers instead: its scan is faster for a single query.  Results
 are the same as a search of the query alone with the same seed (every pair's
 random draws are keyed by its database index, never by its batch), which the
 tests check.
@@ -131,6 +133,12 @@ class Server:
                 mq = max(mq, L)
         return batch, total, mq
 
+    def _plain_fits(self, s: _Slot, qlen):
+        b = C.c_size_t()
+        if lib().hs_search_workspace_size(self.db.handle, qlen, self.k, C.byref(b)) != 0:
+            return False
+        return b.value <= s.ws_bytes and lib().hs_ops_capacity(qlen, self.k) <= s.ops_cap
+
     def _launch(self, s: _Slot, batch, total, mq):
         import torch
         nq = len(batch)
@@ -143,13 +151,19 @@ class Server:
             s.d_q[:total].copy_(s.h_q[:total], non_blocking=True)
             s.d_off[:nq + 1].copy_(s.h_off[:nq + 1], non_blocking=True)
             s.d_seed[:nq].copy_(s.h_seed[:nq], non_blocking=True)
-            cap = lib().hs_batch_ops_capacity(nq, total, self.k)
             meta = s.d_meta.data_ptr()
-            check(lib().hs_search_batch_device(
-                self.db.handle, nq, s.d_q.data_ptr(), s.d_off.data_ptr(), s.d_seed.data_ptr(), total, mq,
-                C.byref(self._p), self.k, C.byref(self.tuning) if self.tuning is not None else None,
-                s.stream.cuda_stream, s.ws.data_ptr(), s.ws_bytes, s.d_hits.data_ptr(), s.d_ops.data_ptr(), cap,
-                meta, meta + 8), "hs_search_batch_device")
+            if nq == 1 and self._plain_fits(s, total):
+                check(lib().hs_search_device(
+                    self.db.handle, s.d_q.data_ptr(), total, C.byref(self._p), self.k, batch[0].seed,
+                    s.stream.cuda_stream, s.ws.data_ptr(), s.ws_bytes, s.d_hits.data_ptr(), s.d_ops.data_ptr(),
+                    lib().hs_ops_capacity(total, self.k), meta, None, None, meta + 8), "hs_search_device")
+            else:
+                cap = lib().hs_batch_ops_capacity(nq, total, self.k)
+                check(lib().hs_search_batch_device(
+                    self.db.handle, nq, s.d_q.data_ptr(), s.d_off.data_ptr(), s.d_seed.data_ptr(), total, mq,
+                    C.byref(self._p), self.k, C.byref(self.tuning) if self.tuning is not None else None,
+                    s.stream.cuda_stream, s.ws.data_ptr(), s.ws_bytes, s.d_hits.data_ptr(), s.d_ops.data_ptr(),
+                    cap, meta, meta + 8), "hs_search_batch_device")
             nh = min(self.k, self.db.n)
             nbytes = nq * self.k * HIT_DTYPE.itemsize
             s.h_hits[:nbytes].copy_(s.d_hits[:nbytes], non_blocking=True)

@@ -66,3 +66,18 @@ def test_memory_gate_bounds_every_batch(db):
     assert len(out) == 30
     h0, o0 = P.search(db, qs[-1], 5, seed=7)
     assert np.array_equal(out[-1][0], h0) and np.array_equal(out[-1][1], o0)
+
+
+def test_single_requests_take_the_plain_path(db):
+    """One request at a time: every batch holds one query (run through the
+    plain search entry point on the slot's buffers) and equals the search of
+    that query alone."""
+    rng = np.random.default_rng(3)
+    qs = [synth.residues(rng, int(L)) for L in (20, 256, 900, 2000)]
+    srv = serve.Server(db, k=10, max_batch=8, slots=2, max_total_qlen=4096)
+    out = [srv.submit(q, 11 + i).result(timeout=120) for i, q in enumerate(qs)]
+    srv.close()
+    assert [nq for nq, _ in srv.batches] == [1, 1, 1, 1]
+    for i, q in enumerate(qs):
+        h0, o0 = P.search(db, q, 10, seed=11 + i)
+        assert np.array_equal(out[i][0], h0) and np.array_equal(out[i][1], o0)
