@@ -191,12 +191,14 @@ class Server:
         now = time.perf_counter()
         for i, r in enumerate(batch):
             h = hits[i * self.k:i * self.k + nh].copy()
-            segs = [ops[x["ops_offset"]:x["ops_offset"] + x["ops_len"]] for x in h]
-            o = np.concatenate(segs).astype(np.uint32) if segs else np.zeros(0, np.uint32)
-            pos = 0
-            for j in range(len(h)):
-                h[j]["ops_offset"] = pos
-                pos += h[j]["ops_len"]
+            # the replay packs every query's ops contiguously, in hit order
+            if nh > 0:
+                first = int(h["ops_offset"][0])
+                end = int(h["ops_offset"][-1] + h["ops_len"][-1])
+                o = ops[first:end].astype(np.uint32)
+                h["ops_offset"] -= first
+            else:
+                o = np.zeros(0, np.uint32)
             r.t_done = now
             self.latencies.append(now - r.t_submit)
             r.future.set_result((h, o))
