@@ -56,7 +56,7 @@ size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k)
     b += align256(sizeof(uint32_t) * 2 * (size_t)profile_words(qlen));
     b += align256(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1));
     b += align256(sizeof(uint32_t) * kNumCounters);
-    b += align256(sizeof(uint64_t) * (size_t)kTopkCtas * (std::max(k, 1) + 1));
+    b += align256(sizeof(uint64_t) * (size_t)kTopkCtas * std::max(k, 1));
     b += align256(sizeof(int64_t) * (size_t)std::max(k, 1));
     b += align256(sizeof(int32_t) * (size_t)std::max(k, 1));
     b += align256(sizeof(uint32_t) * (size_t)std::max(k, 1) * (size_t)slot_stride_for(qlen));
@@ -72,7 +72,7 @@ Workspace carve_workspace(void *base, int64_t n, int32_t qlen, int32_t k)
     w.prof = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 2 * (size_t)profile_words(qlen)));
     w.scores = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
     w.counters = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * kNumCounters));
-    w.cand = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * (size_t)kTopkCtas * (std::max(k, 1) + 1)));
+    w.cand = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * (size_t)kTopkCtas * std::max(k, 1)));
     w.hit_idx = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (size_t)std::max(k, 1)));
     w.hit_score = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (size_t)std::max(k, 1)));
     w.slot_stride = slot_stride_for(qlen);
@@ -558,7 +558,7 @@ static size_t batch_layout(int64_t n, int32_t nq, int64_t total_qlen, int32_t ma
     b.prof = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 2 * kNSym * (size_t)(total_qlen + 17 * qq)));
     b.bounds = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (kMaxChunks + 1)));
     b.scores = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * qq * (size_t)std::max<int64_t>(n, 1)));
-    b.cand = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * qq * kTopkCtas * (kk + 1)));
+    b.cand = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * qq * kTopkCtas * kk));
     b.hit_idx = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * qq * kk));
     b.hit_score = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * qq * kk));
     b.slot_stride = slot_stride_for(std::max(max_qlen, 1));

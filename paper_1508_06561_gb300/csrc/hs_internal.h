@@ -57,7 +57,7 @@ struct Workspace {
     uint32_t *prof;                     // [2 * profile words] reversed, then forward query profile
     int32_t *scores;                    // [n] by database index
     uint32_t *counters;                 // [kNumCounters], zeroed per search
-    uint64_t *cand;                     // [topk_ctas * k] per-CTA top-k keys, then [topk_ctas] k-th keys
+    uint64_t *cand;                     // [topk_ctas * k] per-CTA top-k keys
     int64_t *hit_idx;                   // [k] database index of each ranked hit
     int32_t *hit_score;                 // [k]
     uint32_t *slots;                    // [k * slot_stride] replayed ops
@@ -85,7 +85,7 @@ struct BatchLayout {
                                         // replay ticket, then one top-k ticket per query
     unsigned *item_ctrs, *class_counts, *replay_ticket, *topk_tickets;
     int32_t *qlist;                     // [2][nq] queries of each length class
-    uint64_t *cand;                     // [nq][kTopkCtas * (k + 1)]
+    uint64_t *cand;                     // [nq][kTopkCtas * k]
     int64_t *hit_idx;                   // [nq * k]
     int32_t *hit_score;                 // [nq * k]
     uint32_t *slots;                    // [nq * k][slot_stride]

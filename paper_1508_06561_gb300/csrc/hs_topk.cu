@@ -3,14 +3,14 @@
 // ascending.  Each pair becomes the 64-bit key
 //     ((score ^ 0x80000000) << 32) | (0xFFFFFFFF - index)
 // so a larger key is a better hit and all keys are distinct.  Every CTA
-// selects the k largest keys of its slice and publishes them with its k-th
-// key: the threshold score comes from 12-bit digit histograms of the score
-// above the slice minimum (one pass when the slice's scores span less than
-// 4096 values), ties at the threshold go to the lowest indices.  The global k-th key
-// is at least every full slice's k-th key, so the last CTA to finish keeps
-// only the candidates at or above the largest of those (one pass; at least
-// k of them), sorts them in shared memory and writes the ranked (index,
-// score) list; if they do not fit, it radix-selects over all candidates.
+// selects the k largest keys of its slice: the threshold score comes from
+// 12-bit digit histograms of the score above the slice minimum (one pass
+// when the slice's scores span less than 4096 values), ties at the threshold
+// go to the lowest indices.  The last CTA to finish finds the k-th score of
+// all candidates from one histogram of their scores, sorts the candidates at
+// or above it in shared memory and writes the ranked (index, score) list;
+// for wide score ranges or too many ties it radix-selects over all
+// candidates instead.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -131,10 +131,40 @@ static_assert(kBins % kTopkThreads == 0, "histogram bins split evenly over the t
 struct SliceSmem {
     uint32_t umin, umax;
     uint32_t wsum[kTopkThreads / 32];
-    uint32_t bin, above;
+    uint32_t bin, above, at_bin;
     uint32_t count, ties;
     uint64_t kth;
 };
+
+// The histogram bin holding the `remaining`-th largest key: sets ss.bin and
+// ss.above (the keys in the bins above it).  Thread t owns bins
+// [t * kBinsPerThread, (t + 1) * kBinsPerThread); suffix sums run over the
+// threads.  Ends with a barrier.
+__device__ void find_bin(const uint32_t *hist, uint32_t remaining, SliceSmem &ss)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nw = kTopkThreads / 32;
+    const int b0 = threadIdx.x * kBinsPerThread;
+    uint32_t tot = 0u;
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; j++) tot += hist[b0 + j];
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(0xFFFFFFFFu, incl, o);
+        if (lane + o < 32) incl += y;
+    }
+    if (lane == 0) ss.wsum[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - tot;
+    for (int w = warp + 1; w < nw; w++) run += ss.wsum[w];
+    for (int j = kBinsPerThread - 1; j >= 0; j--) {
+        const uint32_t c = hist[b0 + j];
+        if (run < remaining && run + c >= remaining) { ss.bin = (uint32_t)(b0 + j); ss.above = run; }
+        run += c;
+    }
+    __syncthreads();
+}
 
 // The kk largest keys of the slice [lo, lo + m) of the scores into out[0,
 // kk) (any order); returns the smallest of them.  u = score ^ 0x80000000 is
@@ -171,27 +201,7 @@ __device__ uint64_t slice_select(const int32_t *scores, int64_t lo, int64_t m, u
             if ((((uint64_t)(d ^ prefix)) & hi_mask) == 0) atomicAdd(&hist[(d >> shift) & (kBins - 1)], 1u);
         }
         __syncthreads();
-        // keys in bins above each thread's bins: suffix sums over threads
-        const int b0 = threadIdx.x * kBinsPerThread;
-        uint32_t tot = 0u;
-#pragma unroll
-        for (int j = 0; j < kBinsPerThread; j++) tot += hist[b0 + j];
-        uint32_t incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_down_sync(0xFFFFFFFFu, incl, o);
-            if (lane + o < 32) incl += y;
-        }
-        if (lane == 0) ss.wsum[warp] = incl;
-        __syncthreads();
-        uint32_t run = incl - tot;
-        for (int w = warp + 1; w < nw; w++) run += ss.wsum[w];
-        for (int j = kBinsPerThread - 1; j >= 0; j--) {
-            const uint32_t c = hist[b0 + j];
-            if (run < remaining && run + c >= remaining) { ss.bin = (uint32_t)(b0 + j); ss.above = run; }
-            run += c;
-        }
-        __syncthreads();
+        find_bin(hist, remaining, ss);
         prefix |= ss.bin << shift;
         remaining -= ss.above;
         __syncthreads();                            // ss.bin is read before the next pass sets it
@@ -227,9 +237,8 @@ __device__ uint64_t slice_select(const int32_t *scores, int64_t lo, int64_t m, u
     return ss.kth;
 }
 
-// Batched: blockIdx.y is the query; its scores, candidates (gridDim.x * k
-// keys, then gridDim.x k-th keys), hits and ticket sit at y * n,
-// y * gridDim.x * (k + 1), y * hit_stride and y.
+// Batched: blockIdx.y is the query; its scores, candidates, hits and ticket
+// sit at y * n, y * (gridDim.x * k), y * hit_stride and y.
 __global__ void __launch_bounds__(kTopkThreads)
 topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t *hit_idx,
             int32_t *hit_score, uint32_t *ticket, int32_t hit_stride)
@@ -243,8 +252,7 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
     uint64_t *sortbuf = buf.sortbuf;
     __shared__ int is_last;
     scores += (int64_t)blockIdx.y * n;
-    cand += (int64_t)blockIdx.y * gridDim.x * (k + 1);
-    uint64_t *kths = cand + (int64_t)gridDim.x * k;
+    cand += (int64_t)blockIdx.y * gridDim.x * k;
     hit_idx += (int64_t)blockIdx.y * hit_stride;
     hit_score += (int64_t)blockIdx.y * hit_stride;
     ticket += blockIdx.y;
@@ -256,13 +264,7 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
     uint64_t *mine = cand + (int64_t)blockIdx.x * k;
     for (int i = threadIdx.x; i < k; i += blockDim.x) mine[i] = 0;
     __syncthreads();
-    uint64_t bound = 0;                     // a lower bound of the global k-th key (0: none)
-    if (m > 0) {
-        const uint32_t kk = (uint32_t)min((int64_t)k, m);
-        const uint64_t kth = slice_select(scores, lo, m, kk, mine, buf.hist, ss);
-        if (m >= k) bound = kth;
-    }
-    if (threadIdx.x == 0) kths[blockIdx.x] = bound;
+    if (m > 0) slice_select(scores, lo, m, (uint32_t)min((int64_t)k, m), mine, buf.hist, ss);
 
     __threadfence();
     __syncthreads();
@@ -271,33 +273,60 @@ topk_kernel(const int32_t *scores, int64_t n, int32_t k, uint64_t *cand, int64_t
     if (!is_last) return;
     __threadfence();
 
-    // phase 2: the k best of all candidates, sorted
+    // phase 2: the k best of all candidates, sorted.  The candidates' scores
+    // span a narrow range: their histogram gives the k-th score, and the
+    // candidates at or above it (the k best plus any ties at that score) are
+    // sorted in shared memory.  Wide ranges or too many ties: radix select.
     const int64_t mc = (int64_t)gridDim.x * k;
     const uint32_t kk = (uint32_t)min((int64_t)k, n);
-    if (threadIdx.x == 0) { sm.prefix = 0; sm.count = 0; }
-    __syncthreads();
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
-        atomicMax(reinterpret_cast<unsigned long long *>(&sm.prefix), (unsigned long long)__ldcg(kths + c));
-    __syncthreads();
-    const uint64_t floor_key = sm.prefix;   // the largest slice k-th key
+    const int lane = threadIdx.x & 31;
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
     for (int64_t i = threadIdx.x; i < mc; i += blockDim.x) {
         const uint64_t x = __ldcg(cand + i);
-        if (x != 0 && x >= floor_key) {
-            const uint32_t at = atomicAdd(&sm.count, 1u);
-            if (at < (uint32_t)kSortMax) sortbuf[at] = x;
+        if (x != 0) {
+            mn = min(mn, (uint32_t)(x >> 32));
+            mx = max(mx, (uint32_t)(x >> 32));
         }
     }
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if (threadIdx.x == 0) { ss.umin = 0xFFFFFFFFu; ss.umax = 0u; ss.count = 0u; }
     __syncthreads();
-    const uint32_t kept = sm.count;
+    if (lane == 0) { atomicMin(&ss.umin, mn); atomicMax(&ss.umax, mx); }
+    __syncthreads();
+    const uint32_t umin = ss.umin;
+    bool sorted_here = false;
     int pow2 = 1;
-    if (kept <= (uint32_t)kSortMax) {
-        while (pow2 < (int)kept) pow2 <<= 1;
-        for (int i = (int)kept + threadIdx.x; i < pow2; i += blockDim.x) sortbuf[i] = 0;
+    if (ss.umax - umin < (uint32_t)kBins) {
+        uint32_t *hist = buf.hist;
+        for (int b = threadIdx.x; b < kBins; b += blockDim.x) hist[b] = 0u;
         __syncthreads();
-    } else {
-        // more than fit: select the k-th key over all candidates, keep k
+        for (int64_t i = threadIdx.x; i < mc; i += blockDim.x) {
+            const uint64_t x = __ldcg(cand + i);
+            if (x != 0) atomicAdd(&hist[(uint32_t)(x >> 32) - umin], 1u);
+        }
+        __syncthreads();
+        find_bin(hist, kk, ss);
+        if (threadIdx.x == 0) ss.at_bin = hist[ss.bin];
+        __syncthreads();
+        const uint32_t keep = ss.above + ss.at_bin;     // the candidates at or above the k-th score
+        if (keep <= (uint32_t)kSortMax) {
+            const uint32_t thr = umin + ss.bin;
+            while (pow2 < (int)keep) pow2 <<= 1;
+            __syncthreads();                            // the histogram (sharing sortbuf's memory) is done
+            for (int64_t i = threadIdx.x; i < mc; i += blockDim.x) {
+                const uint64_t x = __ldcg(cand + i);
+                if (x != 0 && (uint32_t)(x >> 32) >= thr) sortbuf[atomicAdd(&ss.count, 1u)] = x;
+            }
+            for (int i = (int)keep + threadIdx.x; i < pow2; i += blockDim.x) sortbuf[i] = 0;
+            __syncthreads();
+            sorted_here = true;
+        }
+    }
+    if (!sorted_here) {
         CandKeys ck{cand};
         const uint64_t kth = radix_kth(ck, mc, kk, sm);
+        pow2 = 1;
         while (pow2 < (int)kk) pow2 <<= 1;
         for (int i = threadIdx.x; i < pow2; i += blockDim.x) sortbuf[i] = 0;
         __syncthreads();
