@@ -64,7 +64,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             if err:
                 print(err)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results]
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-Xlinker",
+                             "--version-script=" + os.path.join(CSRC, "exports.map"), "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

@@ -11,6 +11,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hs_internal.h"
 
 namespace hs {
@@ -48,6 +50,16 @@ static const char kLetters[kNSym + 1] = "ARNDCQEGHILKMFPSTWYVBZX*";
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// NVTX ranges around the host side of each phase (load, search, and the
+// enqueue of profile+scan, top-k and replay), for timeline profilers; free
+// when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 int64_t slot_stride_for(int32_t qlen) { return 2LL * qlen + 4; }
 
 size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k)
@@ -81,6 +93,28 @@ Workspace carve_workspace(void *base, int64_t n, int32_t qlen, int32_t k)
     w.topk_ctas = kTopkCtas;
     w.k = k;
     return w;
+}
+
+// Fault injection for tests: while HS_FAIL_ALLOC is set (non-empty) in the
+// environment, every allocation the library makes fails as if memory were
+// exhausted, so the HS_ENOMEM paths can be exercised without exhausting a
+// GPU.  They release what they took and leave handles usable.
+static bool alloc_refused()
+{
+    const char *v = std::getenv("HS_FAIL_ALLOC");
+    return v && *v;
+}
+
+template <class T> static cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    if (alloc_refused()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+template <class T> static cudaError_t host_malloc(T **p, size_t bytes)
+{
+    if (alloc_refused()) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, bytes);
 }
 
 static int from_cuda(cudaError_t e)
@@ -225,6 +259,7 @@ int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, voi
 int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, int64_t index_base,
                      void *stream, hs_db **out)
 {
+    NvtxRange r("hs_db_load");
     if (index_base < 0 || index_base > (int64_t)INT32_MAX) return HS_EINVAL;
     if (!out || !offsets || n_seqs < 0 || n_seqs > INT32_MAX - 1) return HS_EINVAL;
     *out = nullptr;
@@ -241,7 +276,7 @@ int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seq
     for (int64_t i = 0; i < nres; i++)
         if (codes[i] >= kNSym) return HS_EINVAL;
 
-    hs_db *db = new (std::nothrow) hs_db();
+    hs_db *db = alloc_refused() ? nullptr : new (std::nothrow) hs_db();
     if (!db) return HS_ENOMEM;
     db->n = n_seqs;
     db->nres = nres;
@@ -255,10 +290,10 @@ int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seq
     db->lens.resize((size_t)n_seqs);
     for (int64_t i = 0; i < n_seqs; i++) db->lens[i] = (int32_t)(offsets[i + 1] - offsets[i]);
 
-    e = cudaMalloc(&db->d_codes, (size_t)nres + kCodesPad);
-    if (e == cudaSuccess) e = cudaMalloc(&db->d_offsets, sizeof(int64_t) * (size_t)(n_seqs + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&db->d_order, sizeof(int32_t) * (size_t)std::max<int64_t>(n_seqs, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&db->d_cumres, sizeof(int64_t) * (size_t)(n_seqs + 1));
+    e = dev_malloc(&db->d_codes, (size_t)nres + kCodesPad);
+    if (e == cudaSuccess) e = dev_malloc(&db->d_offsets, sizeof(int64_t) * (size_t)(n_seqs + 1));
+    if (e == cudaSuccess) e = dev_malloc(&db->d_order, sizeof(int32_t) * (size_t)std::max<int64_t>(n_seqs, 1));
+    if (e == cudaSuccess) e = dev_malloc(&db->d_cumres, sizeof(int64_t) * (size_t)(n_seqs + 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(db->d_codes + nres, 0, kCodesPad, st);
     if (e == cudaSuccess && nres > 0) e = cudaMemcpyAsync(db->d_codes, codes, (size_t)nres, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_offsets, offsets, sizeof(int64_t) * (size_t)(n_seqs + 1), cudaMemcpyHostToDevice, st);
@@ -377,14 +412,22 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
         tr.stop = static_cast<cudaEvent_t>(db->trace->scan_stop);
     }
     int launches = 0;
-    e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st, db->trace ? &tr : nullptr,
-                    &launches, input_order);
-    if (e == cudaSuccess && d_count)
-        e = launch_count_at_least(ws.scores, db->n, min_score, d_count, db->num_sms, st, &launches);
-    if (e == cudaSuccess && nhits > 0) e = launch_topk(ws, db->n, nhits, st, &launches);
-    if (e == cudaSuccess && nhits > 0)
+    {
+        NvtxRange r("hs.scan");
+        e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st, db->trace ? &tr : nullptr,
+                        &launches, input_order);
+        if (e == cudaSuccess && d_count)
+            e = launch_count_at_least(ws.scores, db->n, min_score, d_count, db->num_sms, st, &launches);
+    }
+    if (e == cudaSuccess && nhits > 0) {
+        NvtxRange r("hs.topk");
+        e = launch_topk(ws, db->n, nhits, st, &launches);
+    }
+    if (e == cudaSuccess && nhits > 0) {
+        NvtxRange r("hs.replay");
         e = launch_replay(v, d_query, kp, ws, nhits, d_hits, d_ops, ops_cap, d_ops_used, d_status, st,
                           &launches);
+    }
     if (db->trace) db->trace->launches = launches;
     return from_cuda(e);
 }
@@ -394,6 +437,7 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen, cons
                      uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used, int32_t *d_scores,
                      int64_t *d_cells, int32_t *d_status)
 {
+    NvtxRange r("hs_search_device");
     return run_search(db, d_query, qlen, p, k, seed, INT_MIN, stream, d_workspace, ws_bytes, d_hits, d_ops,
                       ops_cap, d_ops_used, d_scores, d_cells, d_status, nullptr);
 }
@@ -420,7 +464,7 @@ static int ensure_host_state(hs_db *db, size_t ws_need, size_t io_need)
         cudaFree(db->d_ws);
         db->d_ws = nullptr;
         db->ws_bytes = 0;
-        e = cudaMalloc(&db->d_ws, ws_need);
+        e = dev_malloc(&db->d_ws, ws_need);
         if (e != cudaSuccess) return from_cuda(e);
         db->ws_bytes = ws_need;
     }
@@ -428,7 +472,7 @@ static int ensure_host_state(hs_db *db, size_t ws_need, size_t io_need)
         cudaFree(db->d_io);
         db->d_io = nullptr;
         db->io_bytes = 0;
-        e = cudaMalloc(&db->d_io, io_need);
+        e = dev_malloc(&db->d_io, io_need);
         if (e != cudaSuccess) return from_cuda(e);
         db->io_bytes = io_need;
     }
@@ -436,7 +480,7 @@ static int ensure_host_state(hs_db *db, size_t ws_need, size_t io_need)
         if (db->h_io) cudaFreeHost(db->h_io);
         db->h_io = nullptr;
         db->h_io_bytes = 0;
-        e = cudaMallocHost(&db->h_io, io_need);
+        e = host_malloc(&db->h_io, io_need);
         if (e != cudaSuccess) return from_cuda(e);
         db->h_io_bytes = io_need;
     }
@@ -467,6 +511,7 @@ static int run_host_search(hs_db *db, const uint8_t *query, int32_t qlen, const 
                            int32_t *n_hits_out, uint32_t *ops_out, int64_t ops_cap, int64_t *ops_used,
                            int64_t *n_above)
 {
+    NvtxRange r(threshold ? "hs_search_threshold" : "hs_search");
     if (!db || !query || !p || !n_hits_out || !ops_used) return HS_EINVAL;
     if (qlen < 1) return HS_EINVAL;
     if (qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
@@ -597,6 +642,7 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
                            size_t ws_bytes, hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap,
                            int64_t *d_ops_used, int32_t *d_status)
 {
+    NvtxRange r("hs_search_batch_device");
     if (!db || !p || !d_workspace || !d_status || nq < 0) return HS_EINVAL;
     if (nq > 0 && (!d_queries || !d_qoffsets || !d_seeds)) return HS_EINVAL;
     if (max_qlen < 1 || total_qlen < nq) return HS_EINVAL;

@@ -90,6 +90,7 @@ class Server:
         self.batches = []                       # (queries, letters) of every batch launched
         self.latencies = []                     # seconds from submit to result, per request
         self.errors = []
+        self.cancelled = 0                      # requests dropped because their caller cancelled them
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -120,15 +121,24 @@ class Server:
         return b.value <= self.slots[0].ws_bytes
 
     def _admit(self):
-        """Requests from the head of the queue that fit one slot's memory."""
+        """Requests from the head of the queue that fit one slot's memory;
+        requests their callers cancelled are dropped here."""
         batch, total, mq = [], 0, 0
         with self.cv:
             while self.queue:
                 r = self.queue[0]
+                if r.future.cancelled():
+                    self.queue.popleft()
+                    self.cancelled += 1
+                    continue
                 L = len(r.query)
                 if not self._fits(len(batch) + 1, total + L, max(mq, L)):
                     break
-                batch.append(self.queue.popleft())
+                self.queue.popleft()
+                if not r.future.set_running_or_notify_cancel():     # cancelled just now
+                    self.cancelled += 1
+                    continue
+                batch.append(r)
                 total += L
                 mq = max(mq, L)
         return batch, total, mq

@@ -39,6 +39,20 @@ def test_every_declared_symbol_is_exported(L):
         assert hasattr(L, name), name
 
 
+def test_exports_are_exactly_the_header(L):
+    """The shared library's dynamic symbol table holds the C ABI and nothing
+    else (internal C++ symbols stay local)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if not nm:
+        pytest.skip("nm not available")
+    from paper_1508_06561_gb300 import build
+    out = subprocess.run([nm, "-D", "--defined-only", build.LIB], capture_output=True, text=True, check=True).stdout
+    exported = sorted({line.split()[-1] for line in out.splitlines() if line.split()[1:2] and line.split()[1] in "TW"})
+    assert exported == declared_functions()
+
+
 def test_builtin_matrix_equals_oracle_table(L):
     assert np.array_equal(P.builtin_matrix(), O.blosum62())
 

@@ -81,3 +81,18 @@ def test_single_requests_take_the_plain_path(db):
     for i, q in enumerate(qs):
         h0, o0 = P.search(db, q, 10, seed=11 + i)
         assert np.array_equal(out[i][0], h0) and np.array_equal(out[i][1], o0)
+
+
+def test_cancelled_requests_do_not_disturb_the_rest(db):
+    rng = np.random.default_rng(4)
+    qs = [synth.residues(rng, int(L)) for L in rng.integers(50, 400, 40)]
+    srv = serve.Server(db, k=5, max_batch=8, slots=1, max_total_qlen=4096)
+    futs = [srv.submit(q, 100 + i) for i, q in enumerate(qs)]
+    gone = [i for i in range(5, 40, 3) if futs[i].cancel()]
+    done = {i: f.result(timeout=120) for i, f in enumerate(futs) if i not in gone}
+    srv.close()
+    assert not srv.errors
+    assert srv.cancelled == len(gone)
+    for i in list(done)[::7]:
+        h0, o0 = P.search(db, qs[i], 5, seed=100 + i)
+        assert np.array_equal(done[i][0], h0) and np.array_equal(done[i][1], o0)

@@ -76,7 +76,9 @@ def test_alignment_valid_and_bounded_by_optimum(case):
     if p.pgp == 0 and nq and nt:
         assert s <= O.smith_waterman(q, t, M, p.gop, p.gep)
     assert 0 <= r < p.rounds
-    assert cells >= min(nq, nt) * p.rounds
+    # work bounds: every step scores at least its ss cells, and the steps of a
+    # round tile part of the |large| x |small| matrix (ls <= Lrem, sum ss <= |small|)
+    assert min(nq, nt) * p.rounds <= cells <= p.rounds * nq * nt
 
 
 def test_self_alignment_is_ungapped_diagonal_sum():

@@ -1,0 +1,51 @@
+"""Host logic of the serving loop, without a GPU: admission from the head of
+the queue under the memory gate, cancelled requests dropped (and admitted
+ones marked running, so a late cancel cannot race the result), and the
+latency summary."""
+import threading
+from collections import deque
+
+import numpy as np
+
+from paper_1508_06561_gb300 import serve
+
+
+def fake_server(fits):
+    srv = serve.Server.__new__(serve.Server)
+    srv.queue = deque()
+    srv.cv = threading.Condition()
+    srv.cancelled = 0
+    srv._fits = fits
+    return srv
+
+
+def test_admission_follows_the_gate_and_drops_cancelled():
+    srv = fake_server(lambda nq, total, mq: nq <= 3 and total <= 100)
+    reqs = [serve._Req(np.zeros(L, np.uint8), i) for i, L in enumerate([10, 20, 30, 40, 5, 7])]
+    assert reqs[1].future.cancel()
+    srv.queue.extend(reqs)
+    batch, total, mq = srv._admit()
+    assert [r.seed for r in batch] == [0, 2, 3]          # 10 + 30 + 40 letters, three queries
+    assert (total, mq) == (80, 40)
+    assert srv.cancelled == 1
+    assert all(r.future.running() for r in batch)
+    assert not batch[0].future.cancel()                  # admitted: too late to cancel
+    batch, total, mq = srv._admit()
+    assert [r.seed for r in batch] == [4, 5] and total == 12
+    assert not srv.queue
+
+
+def test_head_of_queue_blocks_when_it_does_not_fit():
+    srv = fake_server(lambda nq, total, mq: total <= 50)
+    reqs = [serve._Req(np.zeros(L, np.uint8), i) for i, L in enumerate([40, 30, 5])]
+    srv.queue.extend(reqs)
+    batch, _, _ = srv._admit()
+    assert [r.seed for r in batch] == [0]                # FIFO: the 5-letter request waits its turn
+    batch, _, _ = srv._admit()
+    assert [r.seed for r in batch] == [1, 2]
+
+
+def test_latency_stats():
+    st = serve.latency_stats([0.001 * i for i in range(1, 101)])
+    assert abs(st["p50_ms"] - 50.5) < 1e-9 and abs(st["p99_ms"] - 99.01) < 1e-6
+    assert serve.latency_stats([])["p50_ms"] is None
