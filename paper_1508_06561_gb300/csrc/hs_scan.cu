@@ -379,7 +379,56 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
     run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
+// The same scan for one role's profile of a long query (one role per launch):
+// one CTA per SM with kWarps warps, the plan and flat-step slots in dynamic
+// shared memory after the profile, so that the SM keeps as many warps as the
+// fused short-query launch although the profile takes most of its memory.
+template <bool P16, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32, 1)
+scan_wide_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
+                 int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
+{
+    extern __shared__ uint4 smem_raw[];
+    const int64_t n16 = qu.smem_words / 4;
+    const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+    __syncthreads();
+    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    Plan *plans = reinterpret_cast<Plan *>(smem_raw + n16);
+    FlatSlots *slots = reinterpret_cast<FlatSlots *>(plans + kWarps * 32);
+    QueryCtx qc;
+    qc.prof_rev = prof + qu.rev_off;
+    qc.prof_fwd = prof + qu.fwd_off;
+    qc.scores = scores;
+    qc.cells = cells_out;
+    const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
+    const int w = threadIdx.x >> 5;
+    run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, threadIdx.x & 31);
+}
+
+constexpr size_t kWarpSlotBytes = 32 * sizeof(Plan) + sizeof(FlatSlots);
+
 typedef void (*ScanKernelFn)(DbView, ScanQueue, const uint32_t *, SParams, int32_t *, int64_t *);
+
+// The widest CTA whose profile and per-warp slots fit one SM's shared memory
+// (0: none; the 8-warp kernel with static slots is used).
+static int wide_warps(int64_t smem_words)
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    const size_t prof = (size_t)smem_words * 4;
+    for (int w : {24, 12})
+        if (prof + w * kWarpSlotBytes <= (size_t)optin) return w;
+    return 0;
+}
+
+static ScanKernelFn pick_wide_kernel(int warps, bool p16)
+{
+    if (warps == 24) return p16 ? scan_wide_kernel<true, 24> : scan_wide_kernel<false, 24>;
+    return p16 ? scan_wide_kernel<true, 12> : scan_wide_kernel<false, 12>;
+}
 
 static ScanKernelFn pick_scan_kernel(bool smem, bool p16)
 {
@@ -481,14 +530,19 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < nq; i++) {
-        const size_t smem = (size_t)qs[i].smem_words * 4;
+        size_t smem = (size_t)qs[i].smem_words * 4;
         const bool staged = qs[i].smem_words > 0;
+        // one role of a long query: the widest CTA that fits
+        const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order && qs[i].rev_off == qs[i].fwd_off
+                             ? wide_warps(qs[i].smem_words) : 0;
         const ScanKernelFn kern = kp.s.mode == HS_MODE_FULL
                                       ? (staged ? scan_full_kernel<true> : scan_full_kernel<false>)
-                                      : pick_scan_kernel(staged, kp.s.pair16 != 0);
+                                      : wide ? pick_wide_kernel(wide, kp.s.pair16 != 0)
+                                             : pick_scan_kernel(staged, kp.s.pair16 != 0);
+        if (wide) smem += wide * kWarpSlotBytes;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int threads = (kp.s.mode == HS_MODE_FULL ? kWarpsPerCta : kScanWarps) * 32;
+        const int threads = (kp.s.mode == HS_MODE_FULL ? kWarpsPerCta : wide ? wide : kScanWarps) * 32;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e != cudaSuccess) return e;
