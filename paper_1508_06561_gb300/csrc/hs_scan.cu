@@ -600,6 +600,8 @@ struct BatchScan {
     int64_t long_end;
     int32_t *scores;                // [nq][n]
     unsigned *item_ctr;
+    int64_t smem_words;             // profile words staged per CTA (wide kernel: slots follow)
+    int32_t chunk_step;             // chunks per work item (wide CTAs take several)
 };
 
 // kSmem (length order): a chunk that straddles its query's role switch is run
@@ -609,18 +611,19 @@ struct BatchScan {
 #ifndef HS_BATCH_MINB
 #define HS_BATCH_MINB 3
 #endif
+// The batched scan's work loop, shared by the 8-warp kernel (slots in static
+// shared memory) and the wide one (slots in dynamic shared memory after the
+// profile).  prof_s: the staged role profile.
 template <bool kSmem, bool P16>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, HS_BATCH_MINB)
-scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
+__device__ __forceinline__ void batch_items(const DbView &db, const BatchScan &bs, const SParams &sp0,
+                                            uint4 *prof_s, Plan *plans, FlatSlots *slots, long long &s_item,
+                                            unsigned &s_pos)
 {
-    extern __shared__ uint4 smem_raw[];
-    __shared__ Plan plans[kWarpsPerCta][32];
-    __shared__ FlatSlots flat_slots[kWarpsPerCta];
-    __shared__ long long s_item;
-    __shared__ unsigned s_pos;
-    const uint32_t *prof_s = reinterpret_cast<const uint32_t *>(smem_raw);
+    const uint32_t *prof_w = reinterpret_cast<const uint32_t *>(prof_s);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int cur_q = -1, cur_role = -1;
-    const long long nitems = (long long)*bs.qcount * bs.nchunk;
+    const int per_q = (bs.nchunk + bs.chunk_step - 1) / bs.chunk_step;     // items per query
+    const long long nitems = (long long)*bs.qcount * per_q;
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = (long long)atomicAdd(bs.item_ctr, 1u);
@@ -629,9 +632,9 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
         __syncthreads();
         const long long item = s_item;
         if (item >= nitems) break;
-        const int ql = (int)(item / bs.nchunk), c = (int)(item - (long long)ql * bs.nchunk);
+        const int ql = (int)(item / per_q), c = (int)(item - (long long)ql * per_q) * bs.chunk_step;
         const int q = bs.qlist[ql];
-        const int64_t b0 = bs.bounds[c], b1 = bs.bounds[c + 1];
+        const int64_t b0 = bs.bounds[c], b1 = bs.bounds[min(c + bs.chunk_step, bs.nchunk)];
         if (b0 < b1) {
             SParams sp = sp0;
             sp.qlen = (int32_t)(bs.qoffsets[q + 1] - bs.qoffsets[q]);
@@ -656,16 +659,16 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
                     if (q != cur_q || role != cur_role) {
                         __syncthreads();                    // the previous profile is no longer read
                         const uint4 *src = reinterpret_cast<const uint4 *>(pg + (role ? words : 0));
-                        for (int64_t i = threadIdx.x; i < words / 4; i += blockDim.x) smem_raw[i] = src[i];
+                        for (int64_t i = threadIdx.x; i < words / 4; i += blockDim.x) prof_s[i] = src[i];
                         cur_q = q;
                         cur_role = role;
                     }
                     if (threadIdx.x == 0) s_pos = 0;
                     __syncthreads();
-                    qc.prof_rev = prof_s;
-                    qc.prof_fwd = prof_s;
+                    qc.prof_rev = prof_w;
+                    qc.prof_fwd = prof_w;
                     const PosQueue pq = {r0, max(r0, min(bs.long_end, r1)), r1, &s_pos};
-                    run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
+                    run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, lane);
                     __syncthreads();                        // all warps are done with s_pos
                 }
             } else {
@@ -673,14 +676,46 @@ scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
                 qc.prof_rev = pg;
                 qc.prof_fwd = pg + words;
                 const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
-                run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
+                run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, lane);
             }
         }
         __syncthreads();
     }
 }
 
+template <bool kSmem, bool P16>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, HS_BATCH_MINB)
+scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
+{
+    extern __shared__ uint4 smem_raw[];
+    __shared__ Plan plans[kWarpsPerCta * 32];
+    __shared__ FlatSlots flat_slots[kWarpsPerCta];
+    __shared__ long long s_item;
+    __shared__ unsigned s_pos;
+    batch_items<kSmem, P16>(db, bs, sp0, smem_raw, plans, flat_slots, s_item, s_pos);
+}
+
+// Long-query class: one CTA per SM of kWarps warps, the slots after the
+// class's largest profile in dynamic shared memory.
+template <bool P16, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32, 1)
+scan_batch_wide_kernel(DbView db, BatchScan bs, SParams sp0)
+{
+    extern __shared__ uint4 smem_raw[];
+    __shared__ long long s_item;
+    __shared__ unsigned s_pos;
+    Plan *plans = reinterpret_cast<Plan *>(smem_raw + bs.smem_words / 4);
+    FlatSlots *slots = reinterpret_cast<FlatSlots *>(plans + kWarps * 32);
+    batch_items<true, P16>(db, bs, sp0, smem_raw, plans, slots, s_item, s_pos);
+}
+
 typedef void (*BatchKernelFn)(DbView, BatchScan, SParams);
+
+static BatchKernelFn pick_batch_wide_kernel(int warps, bool p16)
+{
+    if (warps == 24) return p16 ? scan_batch_wide_kernel<true, 24> : scan_batch_wide_kernel<false, 24>;
+    return p16 ? scan_batch_wide_kernel<true, 12> : scan_batch_wide_kernel<false, 12>;
+}
 
 static BatchKernelFn pick_batch_kernel(bool smem, bool p16)
 {
@@ -736,15 +771,22 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         bs.qlist = bl.qlist + (int64_t)c * bl.nq;
         bs.qcount = bl.class_counts + c;
         bs.item_ctr = bl.item_ctrs + c;
-        const size_t smem = input_order ? 0 : (size_t)profile_words(cls_len) * 4;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        bs.smem_words = input_order ? 0 : profile_words(cls_len);
+        size_t smem = (size_t)bs.smem_words * 4;
+        // the long class: the widest CTA that fits its profile and slots
+        const int wide = c == 1 && !input_order ? wide_warps(bs.smem_words) : 0;
+        bs.chunk_step = wide ? (wide + kWarpsPerCta - 1) / kWarpsPerCta : 1;
+        const BatchKernelFn kc = wide ? pick_batch_wide_kernel(wide, kp.s.pair16 != 0) : kern;
+        if (wide) smem += wide * kWarpSlotBytes;
+        const int threads = (wide ? wide : kWarpsPerCta) * 32;
+        e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerCta * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
-        kern<<<per_sm * num_sms, kWarpsPerCta * 32, smem, st>>>(db, bs, kp.s);
+        kc<<<per_sm * num_sms, threads, smem, st>>>(db, bs, kp.s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         nl++;
