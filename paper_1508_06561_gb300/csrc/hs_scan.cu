@@ -533,7 +533,11 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         size_t smem = (size_t)qs[i].smem_words * 4;
         const bool staged = qs[i].smem_words > 0;
         // one role of a long query: the widest CTA that fits
-        const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order && qs[i].rev_off == qs[i].fwd_off
+#ifndef HS_FUSED_WIDE
+#define HS_FUSED_WIDE 1
+#endif
+        const bool one_role = qs[i].rev_off == qs[i].fwd_off;
+        const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order && (one_role || HS_FUSED_WIDE)
                              ? wide_warps(qs[i].smem_words) : 0;
         const ScanKernelFn kern = kp.s.mode == HS_MODE_FULL
                                       ? (staged ? scan_full_kernel<true> : scan_full_kernel<false>)
@@ -774,7 +778,10 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         bs.smem_words = input_order ? 0 : profile_words(cls_len);
         size_t smem = (size_t)bs.smem_words * 4;
         // the long class: the widest CTA that fits its profile and slots
-        const int wide = c == 1 && !input_order ? wide_warps(bs.smem_words) : 0;
+#ifndef HS_BATCH_SHORT_WIDE
+#define HS_BATCH_SHORT_WIDE 1
+#endif
+        const int wide = (c == 1 || HS_BATCH_SHORT_WIDE) && !input_order ? wide_warps(bs.smem_words) : 0;
         bs.chunk_step = wide ? (wide + kWarpsPerCta - 1) / kWarpsPerCta : 1;
         const BatchKernelFn kc = wide ? pick_batch_wide_kernel(wide, kp.s.pair16 != 0) : kern;
         if (wide) smem += wide * kWarpSlotBytes;
