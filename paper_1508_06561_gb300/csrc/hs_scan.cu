@@ -79,22 +79,22 @@ struct QueryCtx {
 };
 
 struct Lane {                       // one pair held by one lane
-    int64_t d;                      // database index, -1 = empty
+    int32_t d;                      // database index (< 2^31 by hs_db_load), -1 = empty
     const uint8_t *t;
     int32_t nl, ns, qsmall;
     int32_t Lp, Sp, step, score, best, round;
     uint32_t lf, sf;
     int64_t cells;
-    int64_t blk;                    // Philox block cached in w0..w3
+    int32_t blk;                    // Philox block cached in w0..w3
     uint64_t w0, w1, w2, w3;
 };
 
 __device__ __forceinline__ uint32_t lane_draw(Lane &L, const SParams &sp, uint64_t i)
 {
-    const int64_t b = (int64_t)(i >> 4);
+    const int32_t b = (int32_t)(i >> 4);
     if (b != L.blk) {
         uint64_t o[4];
-        philox4x64_10((uint64_t)(L.d + sp.index_base), (uint64_t)L.round, (uint64_t)b, 0, sp.seed, 0, o);
+        philox4x64_10((uint64_t)((int64_t)L.d + sp.index_base), (uint64_t)L.round, (uint64_t)b, 0, sp.seed, 0, o);
         L.w0 = o[0]; L.w1 = o[1]; L.w2 = o[2]; L.w3 = o[3];
         L.blk = b;
     }
