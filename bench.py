@@ -509,7 +509,7 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": int(d2h.value), "steps": n_e2e},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu" if t_alu_us >= t_hbm_us else "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic, "kernel": "scan_kernel",
+                     "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic, "kernel": "scan_wide_kernel",
                      "scan_ms": scan_s * 1000.0, "cells_per_launch": cells_per_search,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "t_roof_us": max(t_alu_us, t_hbm_us), "t_alu_us": t_alu_us, "t_hbm_us": t_hbm_us,
