@@ -305,7 +305,8 @@ __device__ __forceinline__ void plan_grid(Plan &g)
 // (V, k) pair over all chunks comes from two warp reductions.
 template <bool P16>
 __device__ __forceinline__ void coop_scan_t(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
-                                            int flush, int lane, int32_t &vmax, int32_t &kstar)
+                                            int flush, int lane, int32_t &vmax, int32_t &kstar, int pass0 = 0,
+                                            int pass_stride = 1)
 {
     const int nshift = g.ls - g.ss + 1;
     const int niter = g.qsmall ? g.ss + 3 : g.ss;
@@ -317,7 +318,7 @@ __device__ __forceinline__ void coop_scan_t(const uint32_t *prof, int R, int qle
     const int32_t off = bias * g.ss;
     const int sbase = qlen + 3 - g.Sp;
     int32_t bv = INT_MIN, bk = INT_MAX;
-    for (int base = 0; base < nshift; base += 4 * Gk) {
+    for (int base = pass0 * 4 * Gk; base < nshift; base += pass_stride * 4 * Gk) {
         const int k0 = base + 4 * gk;
         const bool live = in_grid && k0 < nshift;
         Acc<P16> A;
@@ -526,6 +527,83 @@ __device__ __forceinline__ int32_t align_round(const PairCtx &c, const SParams &
     }
     score -= kp.pgp * ((nl - Lp) + (ns - Sp));
     if (EMIT && lane == 0) {
+        ow->push(gap_op, nl - Lp);
+        ow->push(tail_small_op, ns - Sp);
+        ow->flush();
+    }
+    return score;
+}
+
+// The whole CTA scans one step: warp w takes passes w, w + nw, ... of the
+// lane grid, and the warps' best (V, k) pairs are reduced through shared
+// memory (red: nw slots), so every thread ends with the step's argmax.
+__device__ __forceinline__ void coop_scan_cta(const uint32_t *prof, int R, int qlen, const Plan &g, int bias,
+                                              int flush, bool pair16, int lane, int warp, int nw, int2 *red,
+                                              int32_t &vmax, int32_t &kstar)
+{
+    int32_t wv, wk;
+    if (pair16) coop_scan_t<true>(prof, R, qlen, g, bias, flush, lane, wv, wk, warp, nw);
+    else coop_scan_t<false>(prof, R, qlen, g, bias, flush, lane, wv, wk, warp, nw);
+    if (lane == 0) red[warp] = make_int2(wv, wk);
+    __syncthreads();
+    vmax = INT_MIN;
+    kstar = INT_MAX;
+    for (int i = 0; i < nw; i++) {
+        const int2 x = red[i];
+        if (x.x > vmax || (x.x == vmax && x.y < kstar)) { vmax = x.x; kstar = x.y; }
+    }
+    __syncthreads();                                // red is rewritten by the next step
+}
+
+// align_round (database-search form) with every step scanned by the whole
+// CTA (coop_scan_cta); all warps keep the same pair state, warp 0's lane 0
+// writes the ops.  Every thread of the CTA must call it.
+template <bool EMIT>
+__device__ __forceinline__ int32_t align_round_cta(const PairCtx &c, const SParams &kp, uint64_t d, int r,
+                                                   int lane, int warp, int nw, int2 *red, int64_t &cells,
+                                                   OpWriter *ow, Span *span)
+{
+    const int32_t nl = c.qsmall ? c.tlen : c.qlen, ns = c.qsmall ? c.qlen : c.tlen;
+    DrawStream ds;
+    ds.init(kp.seed, d + (uint64_t)kp.index_base, (uint64_t)r);
+    uint32_t lf = (uint32_t)(((uint64_t)kp.lf_q16 * ds.get(0)) >> 16);
+    uint32_t sf = (uint32_t)(((uint64_t)kp.sf_q16 * ds.get(1)) >> 16);
+    lf = max(lf, kp.minf_q16);
+    sf = max(sf, kp.minf_q16);
+    int32_t Lp = 0, Sp = 0, score = 0;
+    int64_t t = 0;
+    const bool writer = EMIT && warp == 0 && lane == 0;
+    const uint32_t gap_op = c.qsmall ? HS_OP_D : HS_OP_I;
+    const uint32_t tail_small_op = c.qsmall ? HS_OP_I : HS_OP_D;
+    while (Lp < nl && Sp < ns) {
+        const int32_t Lrem = nl - Lp, Srem = ns - Sp;
+        int32_t ls = (int32_t)(((uint64_t)Lrem * lf) >> 16);
+        ls = max(ls, 1);
+        const uint64_t u = ds.get(2 + (uint64_t)t);
+        int64_t ssw = (int64_t)(((uint64_t)Srem * sf * u) >> 32);
+        const int32_t ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)min(Srem, ls)));
+        int32_t vmax, kstar;
+        Plan g = {c.t, Lp, Sp, ls, ss, c.qsmall ? 1 : 0, 0, 0, 0};
+        plan_grid(g);
+        coop_scan_cta(c.prof, c.S, c.qlen, g, kp.bias, kp.flush, kp.pair16 != 0, lane, warp, nw, red, vmax, kstar);
+        cells += (int64_t)(ls - ss + 1) * ss;
+        int32_t gap = 0;
+        if (kstar > 0) gap = (t == 0) ? kp.pgp * kstar : kp.gop + (kstar - 1) * kp.gep;
+        score += vmax - gap;
+        if (writer) {
+            ow->push(gap_op, kstar);
+            ow->push(HS_OP_M, ss);
+            const int32_t qb = c.qsmall ? Sp : Lp + kstar, tb = c.qsmall ? Lp + kstar : Sp;
+            if (span->qb < 0) { span->qb = qb; span->tb = tb; }
+            span->qe = qb + ss;
+            span->te = tb + ss;
+        }
+        Lp += kstar + ss;
+        Sp += ss;
+        t++;
+    }
+    score -= kp.pgp * ((nl - Lp) + (ns - Sp));
+    if (writer) {
         ow->push(gap_op, nl - Lp);
         ow->push(tail_small_op, ns - Sp);
         ow->flush();

@@ -834,6 +834,7 @@ struct ReplayArgs {
     int64_t ops_cap;
     int64_t *ops_used;
     int32_t *status;
+    int32_t cta_per_hit;            // one CTA per hit (database form, one round, scan scores given)
 };
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
@@ -843,9 +844,11 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SParams sp0, ReplayArgs ra)
 {
+    __shared__ int2 red[kWarpsPerCta];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int w = blockIdx.x * kWarpsPerCta + warp;     // hit number over all queries
+    const bool cta = ra.cta_per_hit != 0;
+    const int w = cta ? (int)blockIdx.x : (int)blockIdx.x * kWarpsPerCta + warp;     // hit number over all queries
     const int per = max(ra.nhits, 1);
     const int qi = w / per, i = w - qi * per;
     if (ra.nhits > 0 && qi < ra.nq) {
@@ -877,14 +880,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
         } else if (ra.hit_score && sp.rounds == 1) {
             // one round: it is the best one, and the scan's score checks the replay
             best = ra.hit_score[slot];
-            again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span)
-                                            : align_round<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span);
+            if (cta)            // every warp of the CTA scans each step, warp 0 writes the ops
+                again = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, warp, kWarpsPerCta, red, cells, &ow, &span);
+            else
+                again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span)
+                                                : align_round<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span);
         } else {
             best = align_pair(c, sp, (uint64_t)d, lane, cells, &br);
             again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span)
                                             : align_round<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span);
         }
-        if (lane == 0) {
+        if (lane == 0 && (!cta || warp == 0)) {
             if (again != best || (ra.hit_score && ra.hit_score[slot] != best)) set_status(ra.status, HS_EINTERNAL);
             hs_hit h;
             h.db_index = d + sp.index_base;
@@ -973,7 +979,8 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
     ra.ops_cap = ops_cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    const int grid = (nhits + kWarpsPerCta - 1) / kWarpsPerCta;
+    ra.cta_per_hit = kp.s.mode == HS_MODE_DB && kp.s.rounds == 1;
+    const int grid = ra.cta_per_hit ? nhits : (nhits + kWarpsPerCta - 1) / kWarpsPerCta;
     replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     if (launches) *launches += 1;
     return cudaGetLastError();
@@ -1003,7 +1010,8 @@ cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const Batch
     ra.ops_used = d_ops_used;
     ra.status = d_status;
     const int64_t total = (int64_t)bl.nq * nhits;
-    const int grid = (int)((total + kWarpsPerCta - 1) / kWarpsPerCta);
+    ra.cta_per_hit = kp.s.mode == HS_MODE_DB && kp.s.rounds == 1;
+    const int grid = (int)(ra.cta_per_hit ? total : (total + kWarpsPerCta - 1) / kWarpsPerCta);
     replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     if (launches) *launches += 1;
     return cudaGetLastError();

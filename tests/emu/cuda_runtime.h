@@ -12,6 +12,9 @@
 #define __align__(x) alignas(x)
 typedef int cudaError_t;
 struct uint4 { unsigned x, y, z, w; };
+struct int2 { int x, y; };
+inline int2 make_int2(int x, int y) { return int2{x, y}; }
+inline void __syncthreads() {}
 typedef void *cudaStream_t;
 typedef void *cudaEvent_t;
 template <class T> inline T __ldg(const T *p) { return *p; }
