@@ -842,12 +842,15 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
     atomicCAS(status, (int32_t)HS_OK, code);
 }
 
+// kCta: one CTA per hit, one round, database form (only that path is
+// compiled in, which keeps the kernel small); otherwise one warp per hit.
+template <bool kCta>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SParams sp0, ReplayArgs ra)
 {
     __shared__ int2 red[kWarpsPerCta];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const bool cta = ra.cta_per_hit != 0;
+    constexpr bool cta = kCta;
     const int w = cta ? (int)blockIdx.x : (int)blockIdx.x * kWarpsPerCta + warp;     // hit number over all queries
     const int per = max(ra.nhits, 1);
     const int qi = w / per, i = w - qi * per;
@@ -877,14 +880,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
         int32_t best, again;
         if (ra.hit_score && ra.hit_score[slot] < sp.min_score) {
             best = again = ra.hit_score[slot];      // below the reporting threshold: no alignment
-        } else if (ra.hit_score && sp.rounds == 1) {
-            // one round: it is the best one, and the scan's score checks the replay
+        } else if constexpr (kCta) {
+            // one round: it is the best one, and the scan's score checks the
+            // replay; every warp scans each step, warp 0 writes the ops
             best = ra.hit_score[slot];
-            if (cta)            // every warp of the CTA scans each step, warp 0 writes the ops
-                again = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, warp, kWarpsPerCta, red, cells, &ow, &span);
-            else
-                again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span)
-                                                : align_round<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span);
+            again = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, warp, kWarpsPerCta, red, cells, &ow, &span);
+        } else if (ra.hit_score && sp.rounds == 1) {
+            best = ra.hit_score[slot];
+            again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span)
+                                            : align_round<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span);
         } else {
             best = align_pair(c, sp, (uint64_t)d, lane, cells, &br);
             again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span)
@@ -980,8 +984,8 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
     ra.ops_used = d_ops_used;
     ra.status = d_status;
     ra.cta_per_hit = kp.s.mode == HS_MODE_DB && kp.s.rounds == 1;
-    const int grid = ra.cta_per_hit ? nhits : (nhits + kWarpsPerCta - 1) / kWarpsPerCta;
-    replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    if (ra.cta_per_hit) replay_kernel<true><<<nhits, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    else replay_kernel<false><<<(nhits + kWarpsPerCta - 1) / kWarpsPerCta, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -1011,8 +1015,8 @@ cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const Batch
     ra.status = d_status;
     const int64_t total = (int64_t)bl.nq * nhits;
     ra.cta_per_hit = kp.s.mode == HS_MODE_DB && kp.s.rounds == 1;
-    const int grid = (int)(ra.cta_per_hit ? total : (total + kWarpsPerCta - 1) / kWarpsPerCta);
-    replay_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    if (ra.cta_per_hit) replay_kernel<true><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    else replay_kernel<false><<<(int)((total + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -1041,7 +1045,7 @@ cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KP
     ra.ops_cap = cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    replay_kernel<<<1, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    replay_kernel<false><<<1, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
     return cudaGetLastError();
 }
 
