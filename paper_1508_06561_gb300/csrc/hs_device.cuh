@@ -426,16 +426,20 @@ __device__ __forceinline__ uint32_t desc_key(const uint32_t *prof_rev, const uin
                        (int)(d.w & 0xFFFFu) + 1, flush);
 }
 
-// The step owning unit u of the flattened list: the last of the 32 rank
-// slots whose first unit is <= u (first units are non-decreasing; a slot
-// with no units shares its first unit with the next one, so the last match
-// always has units).
-__device__ __forceinline__ int flat_owner(const int32_t *u0, int u)
+// The bit of a pass (units base .. base + 31) where the step of one rank
+// begins its units (u0), 0 if it has none or begins elsewhere.
+__device__ __forceinline__ unsigned start_bit(int u0, int units, int base)
 {
-    int i = 0;
-    for (int st = 16; st; st >>= 1)
-        if (u0[i + st] <= u) i += st;
-    return i;
+    const int p = u0 - base;
+    return (units > 0 && p >= 0 && p < 32) ? (1u << p) : 0u;
+}
+
+// The owner (rank) of lane `lane`'s unit in a pass: the owner of the unit
+// before the pass (carry; -1 before the first) plus the step beginnings at or
+// below the lane (starts: the OR of the ranks' start_bit).
+__device__ __forceinline__ int pass_owner(int carry, unsigned starts, int lane)
+{
+    return carry + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
 }
 
 // ---------------------------------------------------------------------------

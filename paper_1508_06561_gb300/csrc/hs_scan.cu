@@ -277,19 +277,28 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             }
             const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
             fs->rank[src] = lane;
-            fs->u0[lane] = incl - ru;
+            fs->u0[lane] = incl - ru;                   // rank `lane`'s first unit
             fs->key[lane] = 0u;
             __syncwarp();
             const int slot = fs->rank[lane];
             if (flat) fs->desc[slot] = flat_desc(g, sp.qlen);
             else if (busy) plans[lane] = g;
             __syncwarp();
+            // Owners without a search: this lane, as rank `lane`, begins its
+            // step's units at incl - ru; one OR over the warp marks the lanes
+            // of a pass where a step begins, and a unit's owner is the last
+            // owner of the previous pass plus the beginnings up to its lane.
+            const int my_u0 = incl - ru;
+            int carry = -1;
             for (int base = 0; base < total; base += 32) {
                 const int u = base + lane;
                 int i = -1;
                 uint32_t key = 0u;
+                const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, start_bit(my_u0, ru, base));
+                const int owner = pass_owner(carry, starts, lane);
+                carry = __shfl_sync(0xFFFFFFFFu, owner, 31);
                 if (u < total) {
-                    i = flat_owner(fs->u0, u);
+                    i = owner;
                     const uint4 d = fs->desc[i];
                     key = desc_key(qc.prof_rev, qc.prof_fwd, R, d, 4 * (u - fs->u0[i]), sp.flush);
                 }

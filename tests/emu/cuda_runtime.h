@@ -19,6 +19,7 @@ typedef void *cudaStream_t;
 typedef void *cudaEvent_t;
 template <class T> inline T __ldg(const T *p) { return *p; }
 inline uint32_t __funnelshift_r(uint32_t lo, uint32_t hi, uint32_t sh) { return (uint32_t)((((uint64_t)hi << 32) | lo) >> (sh & 31)); }
+inline int __popc(unsigned x) { return __builtin_popcount(x); }
 inline int __clz(int x) { return x == 0 ? 32 : __builtin_clz((unsigned)x); }
 using std::min; using std::max;
 inline int __reduce_max_sync(unsigned, int v) { return v; }

@@ -6,7 +6,7 @@
 // buffers end at PROT_NONE guard pages, so a stray read faults.
 // Also checked: the flattened scan's per-chunk keys (their maximum over a
 // step's chunks gives the step's best shift), the same keys through a flat
-// step's packed descriptor, and the owner search.
+// step's packed descriptor, and the owners from the pass start masks.
 // Both accumulator forms are checked: 32-bit sums always, 16-bit pair sums
 // whenever range * (qlen + 3) <= 65535 (the condition the library uses).
 // usage: lane_emu SEED [MIN MAX]   (matrix entries drawn from [MIN, MAX])
@@ -128,16 +128,29 @@ int main(int argc, char **argv) {
     }
     // owner search of the flattened list: random unit counts (many zero)
     for (int trial = 0; trial < 20000; trial++) {
-        int32_t firsts[32];
+        // ranks: flat steps first (1..63 units each), then steps with none
+        int32_t firsts[32], units[32];
         int u0 = 0, owner[32 * 64];
+        const int nflat = (int)(rng() % 33);
         for (int j = 0; j < 32; j++) {
-            int n = rng() % 3 == 0 ? 0 : (int)(rng() % 64);
+            const int n = j < nflat ? 1 + (int)(rng() % 63) : 0;
             firsts[j] = u0;
+            units[j] = n;
             for (int x = 0; x < n; x++) owner[u0 + x] = j;
             u0 += n;
         }
-        for (int u = 0; u < u0; u++)
-            if (flat_owner(firsts, u) != owner[u]) { printf("owner mismatch trial %d unit %d\n", trial, u); return 1; }
+        int carry = -1;
+        for (int base = 0; base < u0; base += 32) {
+            unsigned starts = 0;
+            for (int r = 0; r < 32; r++) starts |= start_bit(firsts[r], units[r], base);
+            int last = -1;
+            for (int lane = 0; lane < 32; lane++) {
+                const int o = pass_owner(carry, starts, lane);
+                if (base + lane < u0 && o != owner[base + lane]) { printf("owner mismatch trial %d unit %d\n", trial, base + lane); return 1; }
+                last = o;
+            }
+            carry = last;
+        }
     }
     printf("emu ok: %ld shift sums checked\n", checks);
     return 0;
