@@ -442,6 +442,14 @@ __device__ __forceinline__ int pass_owner(int carry, unsigned starts, int lane)
     return carry + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
 }
 
+// The first unit of that owner: the last beginning at or below the lane in
+// this pass, else the carried owner's (carry_u0).
+__device__ __forceinline__ int pass_first_unit(int carry_u0, unsigned starts, int base, int lane)
+{
+    const unsigned le = starts & (0xFFFFFFFFu >> (31 - lane));
+    return le ? base + 31 - __clz((int)le) : carry_u0;
+}
+
 // ---------------------------------------------------------------------------
 // Run-length writer for the alignment ops (lane 0 only).
 // ---------------------------------------------------------------------------

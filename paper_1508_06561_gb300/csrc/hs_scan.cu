@@ -133,10 +133,9 @@ __device__ __forceinline__ void lane_settle(Lane &L, const SParams &sp, const Qu
 }
 
 // Per-warp shared slots of the flattened scan, in rank order: each flat
-// step's descriptor, first unit and best key, and each lane's rank.
+// step's descriptor and best key, and each lane's rank.
 struct FlatSlots {
     uint4 desc[32];
-    int32_t u0[32];
     uint32_t key[32];
     int32_t rank[32];
 };
@@ -277,7 +276,6 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             }
             const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
             fs->rank[src] = lane;
-            fs->u0[lane] = incl - ru;                   // rank `lane`'s first unit
             fs->key[lane] = 0u;
             __syncwarp();
             const int slot = fs->rank[lane];
@@ -289,18 +287,20 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             // of a pass where a step begins, and a unit's owner is the last
             // owner of the previous pass plus the beginnings up to its lane.
             const int my_u0 = incl - ru;
-            int carry = -1;
+            int carry = -1, carry_u0 = 0;           // the last unit's owner and its first unit
             for (int base = 0; base < total; base += 32) {
                 const int u = base + lane;
                 int i = -1;
                 uint32_t key = 0u;
                 const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, start_bit(my_u0, ru, base));
                 const int owner = pass_owner(carry, starts, lane);
+                const int first = pass_first_unit(carry_u0, starts, base, lane);
                 carry = __shfl_sync(0xFFFFFFFFu, owner, 31);
+                carry_u0 = __shfl_sync(0xFFFFFFFFu, first, 31);
                 if (u < total) {
                     i = owner;
                     const uint4 d = fs->desc[i];
-                    key = desc_key(qc.prof_rev, qc.prof_fwd, R, d, 4 * (u - fs->u0[i]), sp.flush);
+                    key = desc_key(qc.prof_rev, qc.prof_fwd, R, d, 4 * (u - first), sp.flush);
                 }
                 fold_keys(fs, i, key, lane);
             }

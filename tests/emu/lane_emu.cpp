@@ -139,17 +139,22 @@ int main(int argc, char **argv) {
             for (int x = 0; x < n; x++) owner[u0 + x] = j;
             u0 += n;
         }
-        int carry = -1;
+        int carry = -1, carry_u0 = 0;
         for (int base = 0; base < u0; base += 32) {
             unsigned starts = 0;
             for (int r = 0; r < 32; r++) starts |= start_bit(firsts[r], units[r], base);
-            int last = -1;
+            int last = -1, last_u0 = 0;
             for (int lane = 0; lane < 32; lane++) {
                 const int o = pass_owner(carry, starts, lane);
-                if (base + lane < u0 && o != owner[base + lane]) { printf("owner mismatch trial %d unit %d\n", trial, base + lane); return 1; }
+                const int f = pass_first_unit(carry_u0, starts, base, lane);
+                if (base + lane < u0 && (o != owner[base + lane] || f != firsts[o])) {
+                    printf("owner mismatch trial %d unit %d\n", trial, base + lane); return 1;
+                }
                 last = o;
+                last_u0 = f;
             }
             carry = last;
+            carry_u0 = last_u0;
         }
     }
     printf("emu ok: %ld shift sums checked\n", checks);
