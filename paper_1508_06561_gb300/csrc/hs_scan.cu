@@ -62,14 +62,8 @@ constexpr int kLocalIters = 64;
 // flattened scan (16-bit pair sums): a step joins the unit list when it has
 // at least kFlatMinChunks chunks or at most kFlatMaxIters iterations per
 // chunk; the rest (few long chunks) get the warp's lane grid
-#ifndef HS_FLAT_MIN_CHUNKS
-#define HS_FLAT_MIN_CHUNKS 16
-#endif
-#ifndef HS_FLAT_MAX_ITERS
-#define HS_FLAT_MAX_ITERS 128
-#endif
-constexpr int kFlatMinChunks = HS_FLAT_MIN_CHUNKS;
-constexpr int kFlatMaxIters = HS_FLAT_MAX_ITERS;
+constexpr int kFlatMinChunks = 16;
+constexpr int kFlatMaxIters = 128;
 
 struct QueryCtx {
     const uint32_t *prof_rev;       // profile for pairs where the query is the small sequence
@@ -140,18 +134,11 @@ struct FlatSlots {
     int32_t rank[32];
 };
 
-#ifndef HS_KEY_COMBINE
-#define HS_KEY_COMBINE 1
-#endif
-
 // Fold a pass's unit keys into their steps' keys.  Units of one step sit in
-// adjacent lanes (owner -1: no unit).
+// adjacent lanes (owner -1: no unit).  A pass of one step (the common case
+// after ranking) takes one warp maximum and one atomic.
 __device__ __forceinline__ void fold_keys(FlatSlots *fs, int i, uint32_t key, int lane)
 {
-#if HS_KEY_COMBINE == 0
-    if (i >= 0) atomicMax(&fs->key[i], key);
-#elif HS_KEY_COMBINE == 1
-    // a pass of one step (the common case after ranking): one warp maximum
     const int i0 = __shfl_sync(0xFFFFFFFFu, i, 0);
     if (__all_sync(0xFFFFFFFFu, i == i0)) {
         const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, key);
@@ -159,17 +146,6 @@ __device__ __forceinline__ void fold_keys(FlatSlots *fs, int i, uint32_t key, in
     } else if (i >= 0) {
         atomicMax(&fs->key[i], key);
     }
-#else
-    // segmented maximum over runs of equal owners, one update per run
-    uint32_t k = key;
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t ok = __shfl_down_sync(0xFFFFFFFFu, k, d);
-        const int oi = __shfl_down_sync(0xFFFFFFFFu, i, d);
-        if (lane + d < 32 && oi == i) k = max(k, ok);
-    }
-    const int pi = __shfl_up_sync(0xFFFFFFFFu, i, 1);
-    if (i >= 0 && (lane == 0 || pi != i)) atomicMax(&fs->key[i], k);
-#endif
 }
 
 // Queue positions [begin, end) of the length order; [begin, long_end) long.
@@ -349,22 +325,16 @@ struct ScanQueue {
     int rev_off, fwd_off;           // word offsets of the two role profiles
 };
 
-// Plain scan CTA shape: warps per CTA and the CTAs per SM the register
-// budget is sized for.
-#ifndef HS_SCAN_WARPS
-#define HS_SCAN_WARPS 8
-#endif
-#ifndef HS_SCAN_MINB
-#define HS_SCAN_MINB 3
-#endif
-constexpr int kScanWarps = HS_SCAN_WARPS;
+// The 8-warp scan CTA (static slots, 3 CTAs per SM), used for the
+// database-order schedule; the length-order launches use scan_wide_kernel.
+constexpr int kScanWarps = 8;
 
 // kSmem: the profiles are staged in shared memory (known to the compiler, so
 // every profile read is a shared load); otherwise they are read in place from
 // global memory (database-order schedule with a query too long for both
 // roles to fit).  P16: 16-bit chunk sums (SParams::pair16).
 template <bool kSmem, bool P16>
-__global__ void __launch_bounds__(kScanWarps * 32, HS_SCAN_MINB)
+__global__ void __launch_bounds__(kScanWarps * 32, 3)
 scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
             int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
@@ -541,13 +511,8 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
     for (int i = 0; i < nq; i++) {
         size_t smem = (size_t)qs[i].smem_words * 4;
         const bool staged = qs[i].smem_words > 0;
-        // one role of a long query: the widest CTA that fits
-#ifndef HS_FUSED_WIDE
-#define HS_FUSED_WIDE 1
-#endif
-        const bool one_role = qs[i].rev_off == qs[i].fwd_off;
-        const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order && (one_role || HS_FUSED_WIDE)
-                             ? wide_warps(qs[i].smem_words) : 0;
+        // length order: one CTA per SM, the widest whose profile(s) and slots fit
+        const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order ? wide_warps(qs[i].smem_words) : 0;
         const ScanKernelFn kern = kp.s.mode == HS_MODE_FULL
                                       ? (staged ? scan_full_kernel<true> : scan_full_kernel<false>)
                                       : wide ? pick_wide_kernel(wide, kp.s.pair16 != 0)
@@ -621,9 +586,6 @@ struct BatchScan {
 // as two sub-ranges, each with its role's profile staged, so every profile
 // read is a shared load.  Otherwise (database order, roles mixed) both role
 // profiles are read from global memory.
-#ifndef HS_BATCH_MINB
-#define HS_BATCH_MINB 3
-#endif
 // The batched scan's work loop, shared by the 8-warp kernel (slots in static
 // shared memory) and the wide one (slots in dynamic shared memory after the
 // profile).  prof_s: the staged role profile.
@@ -697,7 +659,7 @@ __device__ __forceinline__ void batch_items(const DbView &db, const BatchScan &b
 }
 
 template <bool kSmem, bool P16>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, HS_BATCH_MINB)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
 scan_batch_kernel(DbView db, BatchScan bs, SParams sp0)
 {
     extern __shared__ uint4 smem_raw[];
@@ -787,10 +749,7 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         bs.smem_words = input_order ? 0 : profile_words(cls_len);
         size_t smem = (size_t)bs.smem_words * 4;
         // the long class: the widest CTA that fits its profile and slots
-#ifndef HS_BATCH_SHORT_WIDE
-#define HS_BATCH_SHORT_WIDE 1
-#endif
-        const int wide = (c == 1 || HS_BATCH_SHORT_WIDE) && !input_order ? wide_warps(bs.smem_words) : 0;
+        const int wide = !input_order ? wide_warps(bs.smem_words) : 0;
         bs.chunk_step = wide ? (wide + kWarpsPerCta - 1) / kWarpsPerCta : 1;
         const BatchKernelFn kc = wide ? pick_batch_wide_kernel(wide, kp.s.pair16 != 0) : kern;
         if (wide) smem += wide * kWarpSlotBytes;
