@@ -3,6 +3,10 @@
 // for one query (plain) or many (batched).
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "hs_device.cuh"
 
 namespace hs {
@@ -228,10 +232,10 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             // units dealt to the 32 lanes, 32 at a time.  Steps are ranked by
             // role and iterations per unit (a bitonic sort across the warp)
             // so that the units sharing a pass have similar trip counts; flat
-            // slot r holds the descriptor, first unit and key of the step of
-            // rank r.  A unit's lane finds its step by binary search over the
-            // first units and scores its chunk; the pass folds the chunk keys
-            // into the steps' keys.
+            // slot r holds the descriptor and key of the step of rank r.  A
+            // unit's lane finds its step from the pass's start mask (below)
+            // and scores its chunk; the pass folds the chunk keys into
+            // the steps' keys.
             const int units = flat ? (g.ls - g.ss + 4) >> 2 : 0;
             const uint32_t iters = (uint32_t)min(g.ss + 3 * g.qsmall, (1 << 24) - 1);
             uint32_t sk = flat ? ((uint32_t)g.qsmall << 30) | (iters << 5) | (uint32_t)lane
@@ -389,14 +393,58 @@ constexpr size_t kWarpSlotBytes = 32 * sizeof(Plan) + sizeof(FlatSlots);
 
 typedef void (*ScanKernelFn)(DbView, ScanQueue, const uint32_t *, SParams, int32_t *, int64_t *);
 
+// Launch configuration queries, cached per device and (kernel, threads,
+// shared memory): the opt-in shared-memory limit, the dynamic shared-memory
+// attribute last set and the resident CTAs per SM.  A search makes the same
+// few launches every time, so after the first one it queries nothing.
+static std::mutex g_launch_mu;
+
+static int smem_optin()
+{
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    cache[dev] = optin;
+    return optin;
+}
+
+// Sets the kernel's dynamic shared-memory limit (when it grows) and returns
+// its resident CTAs per SM for `threads` threads and `smem` bytes.
+static cudaError_t launch_fit(const void *fn, int threads, size_t smem, int *per_sm)
+{
+    static std::map<std::tuple<int, const void *>, size_t> smem_set;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> occ;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    const auto ks = std::make_tuple(dev, fn);
+    auto si = smem_set.find(ks);
+    if (si == smem_set.end() || si->second < smem) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set[ks] = smem;
+    }
+    const auto ko = std::make_tuple(dev, fn, threads, smem);
+    auto oi = occ.find(ko);
+    if (oi != occ.end()) { *per_sm = oi->second; return cudaSuccess; }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    occ[ko] = *per_sm;
+    return cudaSuccess;
+}
+
 // The widest CTA whose profile and per-warp slots fit one SM's shared memory
 // (0: none; the 8-warp kernel with static slots is used).
 static int wide_warps(int64_t smem_words)
 {
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return 0;
+    const int optin = smem_optin();
+    if (optin <= 0) return 0;
     const size_t prof = (size_t)smem_words * 4;
     for (int w : {24, 12})
         if (prof + w * kWarpSlotBytes <= (size_t)optin) return w;
@@ -518,11 +566,9 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
                                       : wide ? pick_wide_kernel(wide, kp.s.pair16 != 0)
                                              : pick_scan_kernel(staged, kp.s.pair16 != 0);
         if (wide) smem += wide * kWarpSlotBytes;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         const int threads = (kp.s.mode == HS_MODE_FULL ? kWarpsPerCta : wide ? wide : kScanWarps) * 32;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        e = launch_fit(reinterpret_cast<const void *>(kern), threads, smem, &per_sm);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         kern<<<per_sm * num_sms, threads, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores, d_cells);
@@ -754,10 +800,8 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         const BatchKernelFn kc = wide ? pick_batch_wide_kernel(wide, kp.s.pair16 != 0) : kern;
         if (wide) smem += wide * kWarpSlotBytes;
         const int threads = (wide ? wide : kWarpsPerCta) * 32;
-        e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, threads, smem);
+        e = launch_fit(reinterpret_cast<const void *>(kc), threads, smem, &per_sm);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
