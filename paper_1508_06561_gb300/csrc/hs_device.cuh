@@ -186,6 +186,9 @@ __device__ __forceinline__ void rev_main(const uint32_t *prof, int R, const uint
         const int ce = min(n, c + 2 * flush);
         uint32_t x = 0, y = 0;
         int i = c;
+        // eight iterations per trip: the letter loads of a trip issue
+        // together (plain scan 1.33 -> 1.29 ms; 16 per trip: 1.31 ms)
+#pragma unroll 4
         for (; i + 1 < ce; i += 2) {
             x += pw[tp[i] * R - i];
             y += pw[tp[i + 1] * R - (i + 1)];
@@ -241,6 +244,7 @@ __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uin
         const int ce = min(n, c + 2 * flush);
         uint32_t x = 0, y = 0;
         int i = c;
+#pragma unroll 4                                    // as in rev_main
         for (; i + 1 < ce; i += 2) {
             x += pw[tp[i] * R + i];
             y += pw[tp[i + 1] * R + i + 1];
