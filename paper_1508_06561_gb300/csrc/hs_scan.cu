@@ -230,15 +230,17 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         if constexpr (P16) {
             // Flattened scan: the chunks of every flat step form one list of
             // units dealt to the 32 lanes, 32 at a time.  Steps are ranked by
-            // role and iterations per unit (a bitonic sort across the warp)
-            // so that the units sharing a pass have similar trip counts; flat
-            // slot r holds the descriptor and key of the step of rank r.  A
+            // role, then by iterations per unit, most first (a bitonic sort
+            // across the warp), so that the units sharing a pass have similar
+            // trip counts and the last pass, the one only partly filled,
+            // holds the shortest units; flat slot r holds the descriptor and
+            // key of the step of rank r.  A
             // unit's lane finds its step from the pass's start mask (below)
             // and scores its chunk; the pass folds the chunk keys into
             // the steps' keys.
             const int units = flat ? (g.ls - g.ss + 4) >> 2 : 0;
             const uint32_t iters = (uint32_t)min(g.ss + 3 * g.qsmall, (1 << 24) - 1);
-            uint32_t sk = flat ? ((uint32_t)g.qsmall << 30) | (iters << 5) | (uint32_t)lane
+            uint32_t sk = flat ? ((uint32_t)g.qsmall << 30) | ((0xFFFFFFu - iters) << 5) | (uint32_t)lane
                                : 0x80000000u | (uint32_t)lane;
             for (int k = 2; k <= 32; k <<= 1) {
                 for (int j = k >> 1; j > 0; j >>= 1) {
