@@ -139,16 +139,18 @@ struct FlatSlots {
 };
 
 // Fold a pass's unit keys into their steps' keys.  Units of one step sit in
-// adjacent lanes (owner -1: no unit).  A pass of one step (the common case
-// after ranking) takes one warp maximum and one atomic.
-__device__ __forceinline__ void fold_keys(FlatSlots *fs, int i, uint32_t key, int lane)
+// adjacent lanes; lanes past the list hold key 0, which no maximum notices.
+// A pass where no step begins after lane 0 (starts: the pass's start mask)
+// has one owner: it takes one warp maximum and one atomic, the others one
+// atomic per unit.
+__device__ __forceinline__ void fold_keys(FlatSlots *fs, unsigned starts, int owner, bool valid, uint32_t key,
+                                          int lane)
 {
-    const int i0 = __shfl_sync(0xFFFFFFFFu, i, 0);
-    if (__all_sync(0xFFFFFFFFu, i == i0)) {
+    if ((starts >> 1) == 0u) {
         const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, key);
-        if (lane == 0) atomicMax(&fs->key[i0], m);
-    } else if (i >= 0) {
-        atomicMax(&fs->key[i], key);
+        if (lane == 0) atomicMax(&fs->key[owner], m);
+    } else if (valid) {
+        atomicMax(&fs->key[owner], key);
     }
 }
 
@@ -272,19 +274,18 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             int carry = -1, carry_u0 = 0;           // the last unit's owner and its first unit
             for (int base = 0; base < total; base += 32) {
                 const int u = base + lane;
-                int i = -1;
+                const bool valid = u < total;
                 uint32_t key = 0u;
                 const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, start_bit(my_u0, ru, base));
                 const int owner = pass_owner(carry, starts, lane);
                 const int first = pass_first_unit(carry_u0, starts, base, lane);
-                carry = __shfl_sync(0xFFFFFFFFu, owner, 31);
-                carry_u0 = __shfl_sync(0xFFFFFFFFu, first, 31);
-                if (u < total) {
-                    i = owner;
-                    const uint4 d = fs->desc[i];
+                carry_u0 = pass_first_unit(carry_u0, starts, base, 31);     // lane 31's, for the next pass
+                carry = pass_owner(carry, starts, 31);
+                if (valid) {
+                    const uint4 d = fs->desc[owner];
                     key = desc_key(qc.prof_rev, qc.prof_fwd, R, d, 4 * (u - first), sp.flush);
                 }
-                fold_keys(fs, i, key, lane);
+                fold_keys(fs, starts, owner, valid, key, lane);
             }
             __syncwarp();
             if (flat) {
