@@ -150,6 +150,10 @@ int main(int argc, char **argv) {
                 if (base + lane < u0 && (o != owner[base + lane] || f != firsts[o])) {
                     printf("owner mismatch trial %d unit %d\n", trial, base + lane); return 1;
                 }
+                // the fold's one-owner test: no step begins after lane 0
+                if ((starts >> 1) == 0u && base + lane < u0 && owner[base + lane] != owner[base]) {
+                    printf("one-owner test wrong trial %d unit %d\n", trial, base + lane); return 1;
+                }
                 last = o;
                 last_u0 = f;
             }
