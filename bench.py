@@ -27,6 +27,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -90,7 +91,7 @@ class ClockSampler:
     def __init__(self, uuid):
         self.uuid = (uuid or "").lower().replace("gpu-", "")
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = os.path.join(tempfile.gettempdir(), "hs_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -112,7 +113,10 @@ class ClockSampler:
         self.f.close()
         sm, mx, reasons, n = [], [], set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as f:
+            lines = f.readlines()
+        os.remove(self.path)
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue

@@ -2,7 +2,8 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into
 ``paper_1508_06561_gb300/libhsearch.so`` with the CUDA runtime linked
-statically, so the library needs nothing but the driver at run time.
+statically, so the library needs nothing but the NVIDIA kernel driver at
+run time.
 """
 from __future__ import annotations
 
