@@ -94,13 +94,14 @@ class ClockSampler:
         self.path = os.path.join(tempfile.gettempdir(), "hs_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
+        self.f = open(self.path, "w")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
                                           "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
+        except OSError:                     # no nvidia-smi: the line says "unsampled"
             self.proc = None
+            self.f.close()
+            os.remove(self.path)
 
     def stop(self):
         if self.proc is None:
