@@ -142,7 +142,8 @@ class ClockSampler:
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ["hs_device.cuh", "hs_scan.cu", "hs_internal.h"]:
-        h.update(open(os.path.join(ROOT, "paper_1508_06561_gb300", "csrc", f), "rb").read())
+        with open(os.path.join(ROOT, "paper_1508_06561_gb300", "csrc", f), "rb") as src:
+            h.update(src.read())
     return h.hexdigest()[:16]
 
 
@@ -159,7 +160,8 @@ def recorded_traffic(workload_name):
     path = os.path.join(ROOT, "profiles", "scan_kernel_%s.md" % workload_name)
     if not os.path.exists(path):
         return None
-    text = open(path).read()
+    with open(path) as f:
+        text = f.read()
     m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != kernel_source_hash():

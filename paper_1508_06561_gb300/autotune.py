@@ -35,7 +35,8 @@ def tune(db: Database, queries, k: int, params: Params | None = None, sample: in
     key = _key(db, queries, k)
     if cache_path and os.path.exists(cache_path):
         try:
-            _CACHE.update(json.load(open(cache_path)))
+            with open(cache_path) as f:
+                _CACHE.update(json.load(f))
         except (OSError, ValueError):
             pass
     if key in _CACHE:
@@ -68,7 +69,8 @@ def tune(db: Database, queries, k: int, params: Params | None = None, sample: in
     _CACHE[key] = best
     if cache_path:
         try:
-            json.dump(_CACHE, open(cache_path, "w"), indent=1)
+            with open(cache_path, "w") as f:
+                json.dump(_CACHE, f, indent=1)
         except OSError:
             pass
     return best, times
