@@ -1,10 +1,20 @@
-// Host stand-in for cuda_runtime.h: lets the lane-level device functions of
-// the scan compile as plain C++ so a CPU test can check their sums and bounds.
-// Warp-wide intrinsics are identities here; only per-lane code is exercised.
+// Host stand-in for cuda_runtime.h: lets the scan's device functions compile
+// as plain C++ so CPU tests can check them.
+//
+// Two modes.  A thread with no warp context (lane_emu: lane-level sums and
+// bounds) sees the warp-wide intrinsics as identities.  A thread that set
+// emu_warp / emu_lane (pairs_emu: the whole pair loop) is one lane of a
+// 32-thread warp run in lockstep: every warp intrinsic posts the lane's
+// value, waits for all 32 lanes, reads what it needs and waits again, so the
+// device code must call them convergently, as it must on the GPU (a lane that
+// skips one leaves the others waiting, and the test times out).
 #pragma once
 #include <cstdint>
 #include <cstddef>
+#include <cstring>
 #include <algorithm>
+#include <condition_variable>
+#include <mutex>
 #define __device__
 #define __host__
 #define __global__
@@ -21,10 +31,8 @@ template <class T> inline T __ldg(const T *p) { return *p; }
 inline uint32_t __funnelshift_r(uint32_t lo, uint32_t hi, uint32_t sh) { return (uint32_t)((((uint64_t)hi << 32) | lo) >> (sh & 31)); }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
 inline int __clz(int x) { return x == 0 ? 32 : __builtin_clz((unsigned)x); }
+inline int __ffs(int x) { return __builtin_ffs(x); }
 using std::min; using std::max;
-inline int __reduce_max_sync(unsigned, int v) { return v; }
-inline int __reduce_min_sync(unsigned, int v) { return v; }
-template <class T> inline T __shfl_xor_sync(unsigned, T v, int) { return v; }
 // byte n of the result is byte (s >> 4n) & 7 of the 8-byte value y:x (x low)
 inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
     uint64_t v = ((uint64_t)y << 32) | x; uint32_t r = 0;
@@ -32,3 +40,79 @@ inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
     return r;
 }
 inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
+
+// ---- lockstep warp ----------------------------------------------------------
+struct EmuWarp {
+    std::mutex mu;
+    std::condition_variable cv;
+    int arrived = 0;
+    uint64_t gen = 0;
+    uint64_t slot[32] = {};
+    void sync() {
+        std::unique_lock<std::mutex> lk(mu);
+        const uint64_t g = gen;
+        if (++arrived == 32) {
+            arrived = 0;
+            gen++;
+            cv.notify_all();
+        } else {
+            cv.wait(lk, [&] { return gen != g; });
+        }
+    }
+};
+inline thread_local EmuWarp *emu_warp = nullptr;
+inline thread_local int emu_lane = 0;
+
+template <class T> inline uint64_t emu_put(T v) { uint64_t b = 0; std::memcpy(&b, &v, sizeof(T)); return b; }
+template <class T> inline T emu_get(uint64_t b) { T v; std::memcpy(&v, &b, sizeof(T)); return v; }
+// every lane posts v; f reads the 32 posted words
+template <class T, class F> inline auto emu_exchange(T v, F f) {
+    EmuWarp &w = *emu_warp;
+    w.slot[emu_lane] = emu_put(v);
+    w.sync();
+    auto r = f(w.slot);
+    w.sync();
+    return r;
+}
+
+template <class T> inline T __shfl_sync(unsigned, T v, int src) {
+    if (!emu_warp) return v;
+    return emu_exchange(v, [&](const uint64_t *s) { return emu_get<T>(s[src & 31]); });
+}
+template <class T> inline T __shfl_up_sync(unsigned, T v, unsigned d) {
+    if (!emu_warp) return v;
+    return emu_exchange(v, [&](const uint64_t *s) { return emu_lane >= (int)d ? emu_get<T>(s[emu_lane - d]) : v; });
+}
+template <class T> inline T __shfl_xor_sync(unsigned, T v, int o) {
+    if (!emu_warp) return v;
+    return emu_exchange(v, [&](const uint64_t *s) { return emu_get<T>(s[(emu_lane ^ o) & 31]); });
+}
+inline unsigned __ballot_sync(unsigned, int p) {
+    if (!emu_warp) return p ? 1u : 0u;
+    return emu_exchange(p ? 1u : 0u, [](const uint64_t *s) {
+        unsigned r = 0;
+        for (int i = 0; i < 32; i++) r |= (s[i] ? 1u : 0u) << i;
+        return r;
+    });
+}
+template <class T, class Op> inline T emu_reduce(T v, Op op) {
+    if (!emu_warp) return v;
+    return emu_exchange(v, [&](const uint64_t *s) {
+        T r = emu_get<T>(s[0]);
+        for (int i = 1; i < 32; i++) r = op(r, emu_get<T>(s[i]));
+        return r;
+    });
+}
+inline unsigned __reduce_or_sync(unsigned, unsigned v) { return emu_reduce(v, [](unsigned a, unsigned b) { return a | b; }); }
+inline int __reduce_max_sync(unsigned, int v) { return emu_reduce(v, [](int a, int b) { return std::max(a, b); }); }
+inline unsigned __reduce_max_sync(unsigned, unsigned v) { return emu_reduce(v, [](unsigned a, unsigned b) { return std::max(a, b); }); }
+inline int __reduce_min_sync(unsigned, int v) { return emu_reduce(v, [](int a, int b) { return std::min(a, b); }); }
+inline unsigned __reduce_min_sync(unsigned, unsigned v) { return emu_reduce(v, [](unsigned a, unsigned b) { return std::min(a, b); }); }
+inline int __all_sync(unsigned, int p) { return emu_reduce(p ? 1 : 0, [](int a, int b) { return a & b; }); }
+inline void __syncwarp(unsigned = 0xFFFFFFFFu) { if (emu_warp) emu_warp->sync(); }
+inline unsigned atomicAdd(unsigned *p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned atomicMax(unsigned *p, unsigned v) {
+    unsigned old = __atomic_load_n(p, __ATOMIC_SEQ_CST);
+    while (old < v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {}
+    return old;
+}

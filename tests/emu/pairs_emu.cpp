@@ -1,0 +1,124 @@
+// Host run of the scan's whole pair loop (run_pairs, the code every scan
+// kernel's warps execute), compiled as plain C++ against the stub
+// cuda_runtime.h next to this file: each warp is 32 threads in lockstep,
+// shared-memory slots are host arrays, the queue counter is a host atomic.
+// The test harness extracts run_pairs and its helpers from csrc/hs_scan.cu
+// into hs_pairs_region.inc (so the code run here is the kernel source
+// itself) and compares the per-pair scores and cell counts this writes with
+// the oracle's.
+//
+// usage: pairs_emu IN OUT
+//   IN  (little-endian): int64 n, int64 nres, int32 qlen, int32 warps,
+//       int32 pgp, gop, gep, rounds, uint32 lf_q16, sf_q16, minf_q16,
+//       uint64 seed, int64 index_base, int8 M[24*24] (M[query][target]),
+//       uint8 codes[nres], int64 offsets[n+1], uint8 query[qlen]
+//   OUT int32 scores[n], int64 cells[n], int32 pair16, int64 long_end
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "hs_device.cuh"
+
+namespace hs {
+#include "hs_pairs_region.inc"
+}
+
+using namespace hs;
+
+template <class T> static bool rd(FILE *f, T *p, size_t n = 1) { return fread(p, sizeof(T), n, f) == n; }
+
+template <bool P16>
+static void run(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
+{
+    std::vector<EmuWarp> ws(warps);
+    std::vector<Plan> plans((size_t)warps * 32);
+    std::vector<FlatSlots> slots(warps);
+    std::vector<std::thread> th;
+    for (int w = 0; w < warps; w++)
+        for (int lane = 0; lane < 32; lane++)
+            th.emplace_back([&, w, lane] {
+                emu_warp = &ws[w];
+                emu_lane = lane;
+                run_pairs<P16>(db, sp, qc, pq, plans.data() + 32 * w, &slots[w], lane);
+            });
+    for (auto &t : th) t.join();
+}
+
+int main(int argc, char **argv)
+{
+    if (argc != 3) { fprintf(stderr, "usage: pairs_emu IN OUT\n"); return 2; }
+    FILE *f = fopen(argv[1], "rb");
+    if (!f) return 2;
+    int64_t n, nres, index_base;
+    int32_t qlen, warps, pgp, gop, gep, rounds;
+    uint32_t lf, sf, minf;
+    uint64_t seed;
+    int8_t M[kNSym * kNSym];
+    bool ok = rd(f, &n) && rd(f, &nres) && rd(f, &qlen) && rd(f, &warps) && rd(f, &pgp) && rd(f, &gop) &&
+              rd(f, &gep) && rd(f, &rounds) && rd(f, &lf) && rd(f, &sf) && rd(f, &minf) && rd(f, &seed) &&
+              rd(f, &index_base) && rd(f, M, sizeof(M));
+    std::vector<uint8_t> codes((size_t)nres + kCodesPad, 0);
+    std::vector<int64_t> offsets((size_t)n + 1);
+    std::vector<uint8_t> q((size_t)qlen);
+    ok = ok && rd(f, codes.data(), (size_t)nres) && rd(f, offsets.data(), (size_t)n + 1) &&
+         rd(f, q.data(), (size_t)qlen);
+    fclose(f);
+    if (!ok) { fprintf(stderr, "short input\n"); return 2; }
+
+    // the library's host setup: length order (longest first), matrix bias,
+    // byte-lane flush interval, accumulator form, both role profiles
+    std::vector<int32_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    auto len = [&](int32_t d) { return offsets[d + 1] - offsets[d]; };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return len(a) > len(b); });
+    int64_t long_end = 0;
+    while (long_end < n && len(order[long_end]) >= kLongLen) long_end++;
+    int lo = 127, hi = -128;
+    for (int i = 0; i < kNSym * kNSym; i++) { lo = std::min<int>(lo, M[i]); hi = std::max<int>(hi, M[i]); }
+    SParams sp = {};
+    sp.bias = -lo;
+    const int range = hi - lo;
+    sp.flush = range == 0 ? 255 : std::max(1, 255 / range);
+    sp.pgp = pgp; sp.gop = gop; sp.gep = gep; sp.rounds = rounds;
+    sp.lf_q16 = lf; sp.sf_q16 = sf; sp.minf_q16 = minf;
+    sp.qlen = qlen;
+    sp.seed = seed;
+    sp.index_base = index_base;
+    sp.min_score = INT_MIN;
+    sp.mode = HS_MODE_DB;
+    sp.pair16 = (int64_t)range * (qlen + 3) <= 65535;
+    const int R = profile_stride(qlen);
+    const int64_t words = profile_words(qlen);
+    std::vector<uint32_t> prof_rev((size_t)words), prof_fwd((size_t)words);
+    for (int a = 0; a < kNSym; a++)
+        for (int s = 0; s < R; s++) {
+            prof_rev[(size_t)a * R + s] = profile_word_value(q.data(), qlen, true, M, sp.bias, a, s);
+            prof_fwd[(size_t)a * R + s] = profile_word_value(q.data(), qlen, false, M, sp.bias, a, s);
+        }
+
+    std::vector<int32_t> scores((size_t)n, INT32_MIN + 1);
+    std::vector<int64_t> cells((size_t)n, -1);
+    unsigned ctr = 0;
+    const DbView db = {codes.data(), offsets.data(), order.data(), n};
+    QueryCtx qc;
+    qc.prof_rev = prof_rev.data();
+    qc.prof_fwd = prof_fwd.data();
+    qc.scores = scores.data();
+    qc.cells = cells.data();
+    const PosQueue pq = {0, long_end, n, &ctr};
+    if (sp.pair16) run<true>(db, sp, qc, pq, warps);
+    else run<false>(db, sp, qc, pq, warps);
+
+    FILE *o = fopen(argv[2], "wb");
+    if (!o) return 2;
+    const int32_t p16 = sp.pair16;
+    fwrite(scores.data(), sizeof(int32_t), (size_t)n, o);
+    fwrite(cells.data(), sizeof(int64_t), (size_t)n, o);
+    fwrite(&p16, sizeof(p16), 1, o);
+    fwrite(&long_end, sizeof(long_end), 1, o);
+    fclose(o);
+    return 0;
+}
