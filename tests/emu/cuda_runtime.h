@@ -7,7 +7,8 @@
 // 32-thread warp run in lockstep: every warp intrinsic posts the lane's
 // value, waits for all 32 lanes, reads what it needs and waits again, so the
 // device code must call them convergently, as it must on the GPU (a lane that
-// skips one leaves the others waiting, and the test times out).
+// skips one leaves the others waiting, and the test times out).  A thread
+// that also set emu_cta waits at __syncthreads for every thread of its CTA.
 #pragma once
 #include <cstdint>
 #include <cstddef>
@@ -24,7 +25,6 @@ typedef int cudaError_t;
 struct uint4 { unsigned x, y, z, w; };
 struct int2 { int x, y; };
 inline int2 make_int2(int x, int y) { return int2{x, y}; }
-inline void __syncthreads() {}
 typedef void *cudaStream_t;
 typedef void *cudaEvent_t;
 template <class T> inline T __ldg(const T *p) { return *p; }
@@ -41,17 +41,16 @@ inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
 }
 inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
 
-// ---- lockstep warp ----------------------------------------------------------
-struct EmuWarp {
+// ---- lockstep warp (and CTA barrier) ----------------------------------------
+struct EmuBarrier {
     std::mutex mu;
     std::condition_variable cv;
-    int arrived = 0;
+    int count = 32, arrived = 0;
     uint64_t gen = 0;
-    uint64_t slot[32] = {};
     void sync() {
         std::unique_lock<std::mutex> lk(mu);
         const uint64_t g = gen;
-        if (++arrived == 32) {
+        if (++arrived == count) {
             arrived = 0;
             gen++;
             cv.notify_all();
@@ -60,8 +59,13 @@ struct EmuWarp {
         }
     }
 };
+struct EmuWarp : EmuBarrier {
+    uint64_t slot[32] = {};
+};
 inline thread_local EmuWarp *emu_warp = nullptr;
 inline thread_local int emu_lane = 0;
+inline thread_local EmuBarrier *emu_cta = nullptr;     // all threads of the emulated CTA
+inline void __syncthreads() { if (emu_cta) emu_cta->sync(); }
 
 template <class T> inline uint64_t emu_put(T v) { uint64_t b = 0; std::memcpy(&b, &v, sizeof(T)); return b; }
 template <class T> inline T emu_get(uint64_t b) { T v; std::memcpy(&v, &b, sizeof(T)); return v; }
