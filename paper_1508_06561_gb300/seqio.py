@@ -8,17 +8,23 @@ large database is read and encoded once and reloaded without parsing.
 """
 from __future__ import annotations
 
+import gzip
+
 import numpy as np
 
 from . import encode
 
 
 def read_fasta(path_or_lines):
-    """(names, codes uint8, offsets int64[n+1]) from a FASTA file path or an
-    iterable of lines.  Sequence lines may wrap; blank lines and '*' stop
-    codons inside a sequence are kept as letters (code 23), whitespace is
-    dropped.  A file with no '>' header is one sequence named ''."""
-    lines = open(path_or_lines) if isinstance(path_or_lines, str) else path_or_lines
+    """(names, codes uint8, offsets int64[n+1]) from a FASTA file path
+    (gzip-compressed when it ends in .gz) or an iterable of lines.  Sequence
+    lines may wrap; blank lines are skipped; '*' stop codons inside a
+    sequence are kept as letters (code 23); whitespace is dropped.  A file
+    with no '>' header is one sequence named ''."""
+    if isinstance(path_or_lines, str):
+        lines = gzip.open(path_or_lines, "rt") if path_or_lines.endswith(".gz") else open(path_or_lines)
+    else:
+        lines = path_or_lines
     names, chunks, lengths = [], [], []
     cur = None
     try:

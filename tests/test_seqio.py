@@ -1,4 +1,6 @@
 """FASTA reading and the packed database file (host only)."""
+import gzip
+
 import numpy as np
 
 import oracle as O
@@ -44,3 +46,12 @@ def test_save_and_load_roundtrip(tmp_path):
     assert np.array_equal(c2, codes) and np.array_equal(o2, offsets) and n2 == names
     seqio.save_db(db, codes, offsets)
     assert seqio.load_db(db)[2] is None
+
+
+def test_gzip_fasta(tmp_path):
+    path = str(tmp_path / "fa.fasta.gz")
+    with gzip.open(path, "wt") as f:
+        f.write(FASTA)
+    plain = seqio.read_fasta(FASTA.splitlines(True))
+    names, codes, offsets = seqio.read_fasta(path)
+    assert names == plain[0] and np.array_equal(codes, plain[1]) and np.array_equal(offsets, plain[2])
