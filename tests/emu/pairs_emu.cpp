@@ -7,9 +7,14 @@
 // itself) and compares the per-pair scores and cell counts this writes with
 // the oracle's.
 //
-// usage: pairs_emu IN OUT
+// With a third argument "whole", each warp instead takes whole
+// pairs from the queue and scores them with align_pair -- the one-warp-per-
+// pair path of the full-slide scan, the replay and hs_get_alignment -- in
+// the mode the input names.
+//
+// usage: pairs_emu IN OUT [whole]
 //   IN  (little-endian): int64 n, int64 nres, int32 qlen, int32 warps,
-//       int32 pgp, gop, gep, rounds, uint32 lf_q16, sf_q16, minf_q16,
+//       int32 pgp, gop, gep, rounds, mode, uint32 lf_q16, sf_q16, minf_q16,
 //       uint64 seed, int64 index_base, int8 M[24*24] (M[query][target]),
 //       uint8 codes[nres], int64 offsets[n+1], uint8 query[qlen]
 //   OUT int32 scores[n], int64 cells[n], int32 pair16, int64 long_end
@@ -47,19 +52,54 @@ static void run(const DbView &db, const SParams &sp, const QueryCtx &qc, const P
     for (auto &t : th) t.join();
 }
 
+// one pair per warp at a time, as the full-slide scan kernel deals them
+static void run_whole(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
+{
+    std::vector<EmuWarp> ws(warps);
+    std::vector<std::thread> th;
+    for (int w = 0; w < warps; w++)
+        for (int lane = 0; lane < 32; lane++)
+            th.emplace_back([&, w, lane] {
+                emu_warp = &ws[w];
+                emu_lane = lane;
+                for (;;) {
+                    long long pos = 0;
+                    if (lane == 0) pos = (long long)pq.begin + (long long)atomicAdd(pq.ctr, 1u);
+                    pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+                    if (pos >= pq.end) break;
+                    const int64_t d = db.order[pos];
+                    PairCtx c;
+                    c.t = db.codes + db.offsets[d];
+                    c.tlen = (int32_t)(db.offsets[d + 1] - db.offsets[d]);
+                    c.qlen = sp.qlen;
+                    c.qsmall = c.tlen >= sp.qlen;
+                    c.prof = c.qsmall ? qc.prof_rev : qc.prof_fwd;
+                    c.S = profile_stride(sp.qlen);
+                    int64_t cells = 0;
+                    const int32_t sc = align_pair(c, sp, (uint64_t)d, lane, cells, nullptr);
+                    if (lane == 0) {
+                        qc.scores[d] = sc;
+                        qc.cells[d] = cells;
+                    }
+                }
+            });
+    for (auto &t : th) t.join();
+}
+
 int main(int argc, char **argv)
 {
-    if (argc != 3) { fprintf(stderr, "usage: pairs_emu IN OUT\n"); return 2; }
+    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole]\n"); return 2; }
+    const bool whole = argc == 4;
     FILE *f = fopen(argv[1], "rb");
     if (!f) return 2;
     int64_t n, nres, index_base;
-    int32_t qlen, warps, pgp, gop, gep, rounds;
+    int32_t qlen, warps, pgp, gop, gep, rounds, mode;
     uint32_t lf, sf, minf;
     uint64_t seed;
     int8_t M[kNSym * kNSym];
     bool ok = rd(f, &n) && rd(f, &nres) && rd(f, &qlen) && rd(f, &warps) && rd(f, &pgp) && rd(f, &gop) &&
-              rd(f, &gep) && rd(f, &rounds) && rd(f, &lf) && rd(f, &sf) && rd(f, &minf) && rd(f, &seed) &&
-              rd(f, &index_base) && rd(f, M, sizeof(M));
+              rd(f, &gep) && rd(f, &rounds) && rd(f, &mode) && rd(f, &lf) && rd(f, &sf) && rd(f, &minf) &&
+              rd(f, &seed) && rd(f, &index_base) && rd(f, M, sizeof(M));
     std::vector<uint8_t> codes((size_t)nres + kCodesPad, 0);
     std::vector<int64_t> offsets((size_t)n + 1);
     std::vector<uint8_t> q((size_t)qlen);
@@ -88,7 +128,7 @@ int main(int argc, char **argv)
     sp.seed = seed;
     sp.index_base = index_base;
     sp.min_score = INT_MIN;
-    sp.mode = HS_MODE_DB;
+    sp.mode = mode;
     sp.pair16 = (int64_t)range * (qlen + 3) <= 65535;
     const int R = profile_stride(qlen);
     const int64_t words = profile_words(qlen);
@@ -109,7 +149,8 @@ int main(int argc, char **argv)
     qc.scores = scores.data();
     qc.cells = cells.data();
     const PosQueue pq = {0, long_end, n, &ctr};
-    if (sp.pair16) run<true>(db, sp, qc, pq, warps);
+    if (whole) run_whole(db, sp, qc, pq, warps);
+    else if (sp.pair16) run<true>(db, sp, qc, pq, warps);
     else run<false>(db, sp, qc, pq, warps);
 
     FILE *o = fopen(argv[2], "wb");

@@ -10,7 +10,9 @@ stub cuda_runtime.h turns every warp intrinsic into a post-and-wait
 exchange).  Per-pair scores and cell counts must equal the oracle's exactly,
 for both accumulator forms, several warps sharing one queue, long targets
 (the one-per-warp phase), empty targets, several rounds and shard offsets.
-A change to the kernel's bookkeeping can so be checked without a GPU.
+The one-warp-per-pair path (align_pair: full-slide mode, replay) runs the
+same way.  A change to the kernel's bookkeeping can so be checked without a
+GPU.
 """
 import os
 import shutil
@@ -56,10 +58,10 @@ def emu(tmp_path_factory):
     return exe, d
 
 
-def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0):
+def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, whole=False):
     exe, d = emu
     n = len(offsets) - 1
-    hdr = struct.pack("<qqiiiiiiIIIQq", n, len(codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds,
+    hdr = struct.pack("<qqiiiiiiiIIIQq", n, len(codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds, p.mode,
                       p.lfactor_q16, p.sfactor_q16, p.minfactor_q16, seed, index_base)
     inp, out = str(d / "in.bin"), str(d / "out.bin")
     with open(inp, "wb") as f:
@@ -68,7 +70,7 @@ def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0):
         f.write(np.ascontiguousarray(codes, np.uint8).tobytes())
         f.write(np.ascontiguousarray(offsets, np.int64).tobytes())
         f.write(np.ascontiguousarray(q, np.uint8).tobytes())
-    subprocess.run([exe, inp, out], check=True, timeout=600)
+    subprocess.run([exe, inp, out] + (["whole"] if whole else []), check=True, timeout=600)
     with open(out, "rb") as f:
         b = f.read()
     scores = np.frombuffer(b, np.int32, n)
@@ -95,8 +97,8 @@ def mixed_db(rng, n_short, long_lens, extra=(0, 1, 2, 3)):
     return synth.db_from_lengths(rng, lengths)
 
 
-def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None):
-    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base)
+def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, whole=False):
+    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, whole)
     ref, refc = oracle_scores(db, q, M, p, seed, index_base)
     bad = np.nonzero(s != ref)[0]
     assert bad.size == 0, "scores differ at %s: %s vs oracle %s" % (bad[:5], s[bad[:5]], ref[bad[:5]])
@@ -150,3 +152,17 @@ def test_shard_offset_keys_the_draws(emu):
     rng = np.random.default_rng(14)
     db = mixed_db(rng, 60, [], extra=())
     check(emu, db, synth.residues(rng, 80), O.blosum62(), O.paper_params(), 4, index_base=123456)
+
+
+@pytest.mark.parametrize("mode", ["db", "full"])
+def test_one_warp_per_pair(emu, mode):
+    """align_pair, one warp per pair: the full-slide mode's scan (readings
+    F1-F4, several rounds) and the database-mode path the replay and
+    hs_get_alignment run."""
+    rng = np.random.default_rng(15 if mode == "db" else 16)
+    db = mixed_db(rng, 80, [2200])
+    if mode == "db":
+        p = O.paper_params(rounds=2)
+    else:
+        p = O.paper_params(rounds=4, mode=O.MODE_FULL, sfactor_q16=65536, lfactor_q16=65536, minfactor_q16=16384)
+    check(emu, db, synth.residues(rng, 60), O.blosum62(), p, 8, warps=3, whole=True)
