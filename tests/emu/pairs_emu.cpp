@@ -10,9 +10,11 @@
 // With a third argument "whole", each warp instead takes whole
 // pairs from the queue and scores them with align_pair -- the one-warp-per-
 // pair path of the full-slide scan, the replay and hs_get_alignment -- in
-// the mode the input names.
+// the mode the input names.  With "cta", one CTA of `warps` warps takes
+// each pair and every step is scanned by all its warps (align_round_cta,
+// the replay's path for one-round searches).
 //
-// usage: pairs_emu IN OUT [whole]
+// usage: pairs_emu IN OUT [whole|cta]
 //   IN  (little-endian): int64 n, int64 nres, int32 qlen, int32 warps,
 //       int32 pgp, gop, gep, rounds, mode, uint32 lf_q16, sf_q16, minf_q16,
 //       uint64 seed, int64 index_base, int8 M[24*24] (M[query][target]),
@@ -22,6 +24,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <numeric>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -86,10 +89,56 @@ static void run_whole(const DbView &db, const SParams &sp, const QueryCtx &qc, c
     for (auto &t : th) t.join();
 }
 
+// one CTA: each pair's steps split over all its warps, rounds in turn
+static void run_cta(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
+{
+    std::vector<EmuWarp> ws(warps);
+    EmuBarrier cta;
+    cta.count = 32 * warps;
+    std::vector<int2> red(warps);
+    long long claim = 0;
+    std::vector<std::thread> th;
+    for (int w = 0; w < warps; w++)
+        for (int lane = 0; lane < 32; lane++)
+            th.emplace_back([&, w, lane] {
+                emu_warp = &ws[w];
+                emu_lane = lane;
+                emu_cta = &cta;
+                const bool lead = w == 0 && lane == 0;
+                for (;;) {
+                    if (lead) claim = (long long)pq.begin + (long long)atomicAdd(pq.ctr, 1u);
+                    __syncthreads();
+                    const long long pos = claim;
+                    __syncthreads();
+                    if (pos >= pq.end) break;
+                    const int64_t d = db.order[pos];
+                    PairCtx c;
+                    c.t = db.codes + db.offsets[d];
+                    c.tlen = (int32_t)(db.offsets[d + 1] - db.offsets[d]);
+                    c.qlen = sp.qlen;
+                    c.qsmall = c.tlen >= sp.qlen;
+                    c.prof = c.qsmall ? qc.prof_rev : qc.prof_fwd;
+                    c.S = profile_stride(sp.qlen);
+                    int64_t cells = 0;
+                    int32_t best = INT_MIN;
+                    for (int r = 0; r < sp.rounds; r++) {
+                        const int32_t sc = align_round_cta<false>(c, sp, (uint64_t)d, r, lane, w, warps, red.data(),
+                                                                  cells, nullptr, nullptr);
+                        if (sc > best) best = sc;
+                    }
+                    if (lead) {
+                        qc.scores[d] = best;
+                        qc.cells[d] = cells;
+                    }
+                }
+            });
+    for (auto &t : th) t.join();
+}
+
 int main(int argc, char **argv)
 {
-    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole]\n"); return 2; }
-    const bool whole = argc == 4;
+    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole|cta]\n"); return 2; }
+    const std::string how = argc == 4 ? argv[3] : "";
     FILE *f = fopen(argv[1], "rb");
     if (!f) return 2;
     int64_t n, nres, index_base;
@@ -149,7 +198,8 @@ int main(int argc, char **argv)
     qc.scores = scores.data();
     qc.cells = cells.data();
     const PosQueue pq = {0, long_end, n, &ctr};
-    if (whole) run_whole(db, sp, qc, pq, warps);
+    if (how == "whole") run_whole(db, sp, qc, pq, warps);
+    else if (how == "cta") run_cta(db, sp, qc, pq, warps);
     else if (sp.pair16) run<true>(db, sp, qc, pq, warps);
     else run<false>(db, sp, qc, pq, warps);
 

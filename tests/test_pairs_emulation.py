@@ -10,8 +10,9 @@ stub cuda_runtime.h turns every warp intrinsic into a post-and-wait
 exchange).  Per-pair scores and cell counts must equal the oracle's exactly,
 for both accumulator forms, several warps sharing one queue, long targets
 (the one-per-warp phase), empty targets, several rounds and shard offsets.
-The one-warp-per-pair path (align_pair: full-slide mode, replay) runs the
-same way.  A change to the kernel's bookkeeping can so be checked without a
+The one-warp-per-pair path (align_pair: full-slide mode, replay) and the
+one-CTA-per-pair path (align_round_cta, with a CTA barrier) run the same
+way.  A change to the kernel's bookkeeping can so be checked without a
 GPU.
 """
 import os
@@ -58,7 +59,7 @@ def emu(tmp_path_factory):
     return exe, d
 
 
-def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, whole=False):
+def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how=""):
     exe, d = emu
     n = len(offsets) - 1
     hdr = struct.pack("<qqiiiiiiiIIIQq", n, len(codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds, p.mode,
@@ -70,7 +71,7 @@ def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, whole=Fal
         f.write(np.ascontiguousarray(codes, np.uint8).tobytes())
         f.write(np.ascontiguousarray(offsets, np.int64).tobytes())
         f.write(np.ascontiguousarray(q, np.uint8).tobytes())
-    subprocess.run([exe, inp, out] + (["whole"] if whole else []), check=True, timeout=600)
+    subprocess.run([exe, inp, out] + ([how] if how else []), check=True, timeout=600)
     with open(out, "rb") as f:
         b = f.read()
     scores = np.frombuffer(b, np.int32, n)
@@ -97,8 +98,8 @@ def mixed_db(rng, n_short, long_lens, extra=(0, 1, 2, 3)):
     return synth.db_from_lengths(rng, lengths)
 
 
-def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, whole=False):
-    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, whole)
+def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, how=""):
+    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how)
     ref, refc = oracle_scores(db, q, M, p, seed, index_base)
     bad = np.nonzero(s != ref)[0]
     assert bad.size == 0, "scores differ at %s: %s vs oracle %s" % (bad[:5], s[bad[:5]], ref[bad[:5]])
@@ -165,4 +166,15 @@ def test_one_warp_per_pair(emu, mode):
         p = O.paper_params(rounds=2)
     else:
         p = O.paper_params(rounds=4, mode=O.MODE_FULL, sfactor_q16=65536, lfactor_q16=65536, minfactor_q16=16384)
-    check(emu, db, synth.residues(rng, 60), O.blosum62(), p, 8, warps=3, whole=True)
+    check(emu, db, synth.residues(rng, 60), O.blosum62(), p, 8, warps=3, how="whole")
+
+
+@pytest.mark.parametrize("matrix", ["blosum62", "full-range"])
+def test_one_cta_per_pair(emu, matrix):
+    """align_round_cta: every step of a pair scanned by all warps of a CTA,
+    their best shifts reduced through shared memory (the replay's path for
+    one-round searches), for both accumulator forms and several rounds."""
+    rng = np.random.default_rng(17 if matrix == "blosum62" else 18)
+    M = O.blosum62() if matrix == "blosum62" else synth.random_symmetric_matrix(rng, -128, 127)
+    db = mixed_db(rng, 60, [2400])
+    check(emu, db, synth.residues(rng, 280), M, O.paper_params(rounds=2), 6, warps=4, how="cta")
