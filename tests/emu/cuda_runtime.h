@@ -8,7 +8,10 @@
 // value, waits for all 32 lanes, reads what it needs and waits again, so the
 // device code must call them convergently, as it must on the GPU (a lane that
 // skips one leaves the others waiting, and the test times out).  A thread
-// that also set emu_cta waits at __syncthreads for every thread of its CTA.
+// that also set emu_cta waits at __syncthreads for every thread of its CTA;
+// threadIdx / blockIdx / blockDim / gridDim are per-thread variables the
+// harness sets, and a kernel's __shared__ variables are function statics,
+// so a harness runs one CTA at a time.
 #pragma once
 #include <cstdint>
 #include <cstddef>
@@ -21,6 +24,9 @@
 #define __global__
 #define __forceinline__ inline
 #define __align__(x) alignas(x)
+#define __launch_bounds__(...)
+// a kernel's shared variables: one copy, so CTAs are run one after another
+#define __shared__ static
 typedef int cudaError_t;
 struct uint4 { unsigned x, y, z, w; };
 struct int2 { int x, y; };
@@ -66,6 +72,10 @@ inline thread_local EmuWarp *emu_warp = nullptr;
 inline thread_local int emu_lane = 0;
 inline thread_local EmuBarrier *emu_cta = nullptr;     // all threads of the emulated CTA
 inline void __syncthreads() { if (emu_cta) emu_cta->sync(); }
+inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+struct EmuDim3 { unsigned x = 0, y = 0, z = 0; };
+inline thread_local EmuDim3 threadIdx, blockIdx, blockDim, gridDim;
+template <class T> inline T __ldcg(const T *p) { return *p; }
 
 template <class T> inline uint64_t emu_put(T v) { uint64_t b = 0; std::memcpy(&b, &v, sizeof(T)); return b; }
 template <class T> inline T emu_get(uint64_t b) { T v; std::memcpy(&v, &b, sizeof(T)); return v; }
@@ -86,6 +96,10 @@ template <class T> inline T __shfl_sync(unsigned, T v, int src) {
 template <class T> inline T __shfl_up_sync(unsigned, T v, unsigned d) {
     if (!emu_warp) return v;
     return emu_exchange(v, [&](const uint64_t *s) { return emu_lane >= (int)d ? emu_get<T>(s[emu_lane - d]) : v; });
+}
+template <class T> inline T __shfl_down_sync(unsigned, T v, unsigned d) {
+    if (!emu_warp) return v;
+    return emu_exchange(v, [&](const uint64_t *s) { return emu_lane + (int)d < 32 ? emu_get<T>(s[emu_lane + d]) : v; });
 }
 template <class T> inline T __shfl_xor_sync(unsigned, T v, int o) {
     if (!emu_warp) return v;
@@ -115,6 +129,11 @@ inline unsigned __reduce_min_sync(unsigned, unsigned v) { return emu_reduce(v, [
 inline int __all_sync(unsigned, int p) { return emu_reduce(p ? 1 : 0, [](int a, int b) { return a & b; }); }
 inline void __syncwarp(unsigned = 0xFFFFFFFFu) { if (emu_warp) emu_warp->sync(); }
 inline unsigned atomicAdd(unsigned *p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned atomicMin(unsigned *p, unsigned v) {
+    unsigned old = __atomic_load_n(p, __ATOMIC_SEQ_CST);
+    while (old > v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {}
+    return old;
+}
 inline unsigned atomicMax(unsigned *p, unsigned v) {
     unsigned old = __atomic_load_n(p, __ATOMIC_SEQ_CST);
     while (old < v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {}
