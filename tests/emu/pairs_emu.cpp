@@ -12,9 +12,14 @@
 // pair path of the full-slide scan, the replay and hs_get_alignment -- in
 // the mode the input names.  With "cta", one CTA of `warps` warps takes
 // each pair and every step is scanned by all its warps (align_round_cta,
-// the replay's path for one-round searches).
+// the replay's path for one-round searches).  With "ops" or "ops_cta" the
+// pairs are replayed as the replay kernel does it -- best round found, then
+// that round run again writing run-length ops, by one warp or (one round)
+// by one CTA -- and OUT gets, per pair in database order, int32 score,
+// int32 ops count, int32 span[4] (q begin, q end, t begin, t end) and the
+// ops.
 //
-// usage: pairs_emu IN OUT [whole|cta]
+// usage: pairs_emu IN OUT [whole|cta|ops|ops_cta]
 //   IN  (little-endian): int64 n, int64 nres, int32 qlen, int32 warps,
 //       int32 pgp, gop, gep, rounds, mode, uint32 lf_q16, sf_q16, minf_q16,
 //       uint64 seed, int64 index_base, int8 M[24*24] (M[query][target]),
@@ -135,9 +140,74 @@ static void run_cta(const DbView &db, const SParams &sp, const QueryCtx &qc, con
     for (auto &t : th) t.join();
 }
 
+// the replay's emission, one warp (cta = false) or one CTA per pair
+struct Replayed {
+    int32_t score = 0;
+    Span span = {-1, -1, -1, -1};
+    std::vector<uint32_t> ops;
+};
+static void run_replay(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps,
+                       bool cta_mode, std::vector<Replayed> &out)
+{
+    const int nw = cta_mode ? warps : 1;         // warps per pair
+    const int groups = cta_mode ? 1 : warps;
+    std::vector<EmuWarp> ws(warps);
+    std::vector<EmuBarrier> bars(groups);
+    for (auto &b : bars) b.count = 32 * nw;
+    std::vector<int2> red(warps);
+    std::vector<long long> claim(groups);
+    std::vector<std::thread> th;
+    for (int w = 0; w < warps; w++)
+        for (int lane = 0; lane < 32; lane++)
+            th.emplace_back([&, w, lane] {
+                const int g = cta_mode ? 0 : w, wi = cta_mode ? w : 0;
+                emu_warp = &ws[w];
+                emu_lane = lane;
+                emu_cta = &bars[g];
+                const bool lead = wi == 0 && lane == 0;
+                for (;;) {
+                    if (lead) claim[g] = (long long)pq.begin + (long long)atomicAdd(pq.ctr, 1u);
+                    __syncthreads();
+                    const long long pos = claim[g];
+                    __syncthreads();
+                    if (pos >= pq.end) break;
+                    const int64_t d = db.order[pos];
+                    PairCtx c;
+                    c.t = db.codes + db.offsets[d];
+                    c.tlen = (int32_t)(db.offsets[d + 1] - db.offsets[d]);
+                    c.qlen = sp.qlen;
+                    c.qsmall = c.tlen >= sp.qlen;
+                    c.prof = c.qsmall ? qc.prof_rev : qc.prof_fwd;
+                    c.S = profile_stride(sp.qlen);
+                    std::vector<uint32_t> buf((size_t)c.tlen + sp.qlen + 8);
+                    OpWriter ow;
+                    ow.init(buf.data(), (int64_t)buf.size());
+                    Span span = {-1, -1, -1, -1};
+                    int64_t cells = 0;
+                    int32_t sc;
+                    if (cta_mode) {
+                        sc = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, wi, nw, red.data(), cells, &ow, &span);
+                    } else {
+                        int br = 0;
+                        align_pair(c, sp, (uint64_t)d, lane, cells, &br);
+                        sc = sp.mode == HS_MODE_FULL
+                                 ? align_round_full<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span)
+                                 : align_round<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span);
+                    }
+                    if (lead) {
+                        Replayed &r = out[d];
+                        r.score = sc;
+                        r.span = span;
+                        r.ops.assign(buf.begin(), buf.begin() + std::min<int64_t>(ow.n, (int64_t)buf.size()));
+                    }
+                }
+            });
+    for (auto &t : th) t.join();
+}
+
 int main(int argc, char **argv)
 {
-    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole|cta]\n"); return 2; }
+    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole|cta|ops|ops_cta]\n"); return 2; }
     const std::string how = argc == 4 ? argv[3] : "";
     FILE *f = fopen(argv[1], "rb");
     if (!f) return 2;
@@ -198,6 +268,19 @@ int main(int argc, char **argv)
     qc.scores = scores.data();
     qc.cells = cells.data();
     const PosQueue pq = {0, long_end, n, &ctr};
+    if (how == "ops" || how == "ops_cta") {
+        std::vector<Replayed> rep((size_t)n);
+        run_replay(db, sp, qc, pq, warps, how == "ops_cta", rep);
+        FILE *o = fopen(argv[2], "wb");
+        if (!o) return 2;
+        for (const Replayed &r : rep) {
+            const int32_t hdr[6] = {r.score, (int32_t)r.ops.size(), r.span.qb, r.span.qe, r.span.tb, r.span.te};
+            fwrite(hdr, sizeof(int32_t), 6, o);
+            fwrite(r.ops.data(), sizeof(uint32_t), r.ops.size(), o);
+        }
+        fclose(o);
+        return 0;
+    }
     if (how == "whole") run_whole(db, sp, qc, pq, warps);
     else if (how == "cta") run_cta(db, sp, qc, pq, warps);
     else if (sp.pair16) run<true>(db, sp, qc, pq, warps);

@@ -12,7 +12,8 @@ for both accumulator forms, several warps sharing one queue, long targets
 (the one-per-warp phase), empty targets, several rounds and shard offsets.
 The one-warp-per-pair path (align_pair: full-slide mode, replay) and the
 one-CTA-per-pair path (align_round_cta, with a CTA barrier) run the same
-way.  A change to the kernel's bookkeeping can so be checked without a
+way, and so does the replay's emission of run-length ops, whose rows must
+equal the oracle's alignment.  A change to the kernel's bookkeeping can so be checked without a
 GPU.
 """
 import os
@@ -178,3 +179,52 @@ def test_one_cta_per_pair(emu, matrix):
     M = O.blosum62() if matrix == "blosum62" else synth.random_symmetric_matrix(rng, -128, 127)
     db = mixed_db(rng, 60, [2400])
     check(emu, db, synth.residues(rng, 280), M, O.paper_params(rounds=2), 6, warps=4, how="cta")
+
+
+def run_replay(emu, db, q, M, p, seed, warps, how):
+    exe, d = emu
+    hdr = struct.pack("<qqiiiiiiiIIIQq", db.n, len(db.codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds, p.mode,
+                      p.lfactor_q16, p.sfactor_q16, p.minfactor_q16, seed, 0)
+    inp, out = str(d / "in.bin"), str(d / "out.bin")
+    with open(inp, "wb") as f:
+        f.write(hdr)
+        f.write(np.ascontiguousarray(M, np.int8).tobytes())
+        f.write(np.ascontiguousarray(db.codes, np.uint8).tobytes())
+        f.write(np.ascontiguousarray(db.offsets, np.int64).tobytes())
+        f.write(np.ascontiguousarray(q, np.uint8).tobytes())
+    subprocess.run([exe, inp, out, how], check=True, timeout=600)
+    with open(out, "rb") as f:
+        b = f.read()
+    res, at = [], 0
+    for _ in range(db.n):
+        score, nops, qb, qe, tb, te = struct.unpack_from("<6i", b, at)
+        at += 24
+        res.append((score, (qb, qe, tb, te), np.frombuffer(b, np.uint32, nops, at)))
+        at += 4 * nops
+    assert at == len(b)
+    return res
+
+
+@pytest.mark.parametrize("how,mode,rounds", [("ops", "db", 3), ("ops", "full", 2), ("ops_cta", "db", 1)])
+def test_replayed_alignments(emu, how, mode, rounds):
+    """The replay's emission -- run-length ops and core span of the best
+    round, by one warp, or by one CTA for one-round searches -- expands to
+    the oracle's alignment rows, rescores to the score, and spans the first
+    to the last letter pair."""
+    from paper_1508_06561_gb300 import ops_to_rows
+    rng = np.random.default_rng(19 + rounds)
+    db = mixed_db(rng, 40, [2100])
+    q = synth.residues(rng, 70)
+    M = O.blosum62()
+    p = O.paper_params(rounds=rounds, pgp=1, mode=O.MODE_FULL if mode == "full" else O.MODE_DB)
+    for d, (score, span, ops) in enumerate(run_replay(emu, db, q, M, p, 2, 3, how)):
+        t = db.seq(d)
+        s, oq, ot, _, _ = O.align_pair(q, t, M, p, 2, d)
+        rq, rt = ops_to_rows(ops, q, t)
+        assert score == s and np.array_equal(rq, oq) and np.array_equal(rt, ot), d
+        assert O.score_rows(rq, rt, M, p.pgp, p.gop, p.gep) == s
+        m = (rq != 255) & (rt != 255)
+        if m.any():
+            cols = np.nonzero(m)[0]
+            qpos, tpos = np.cumsum(rq != 255) - 1, np.cumsum(rt != 255) - 1
+            assert span == (qpos[cols[0]], qpos[cols[-1]] + 1, tpos[cols[0]], tpos[cols[-1]] + 1)
