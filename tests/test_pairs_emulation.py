@@ -228,3 +228,46 @@ def test_replayed_alignments(emu, how, mode, rounds):
             cols = np.nonzero(m)[0]
             qpos, tpos = np.cumsum(rq != 255) - 1, np.cumsum(rt != 255) - 1
             assert span == (qpos[cols[0]], qpos[cols[-1]] + 1, tpos[cols[0]], tpos[cols[-1]] + 1)
+
+
+@pytest.fixture(scope="module")
+def emu_tsan(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("pairs_emu_tsan")
+    with open(d / "hs_pairs_region.inc", "w") as f:
+        f.write(pair_loop_source())
+    exe = str(d / "pairs_emu")
+    r = subprocess.run([gxx, "-O1", "-g", "-fsanitize=thread", "-std=c++17", "-pthread", "-Wno-unknown-pragmas",
+                        "-I", os.path.join(ROOT, "tests", "emu"), "-I", str(d), "-I", CSRC,
+                        "-I", os.path.join(ROOT, "include"), "-o", exe,
+                        os.path.join(ROOT, "tests", "emu", "pairs_emu.cpp")], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("no ThreadSanitizer runtime: " + r.stderr[-200:])
+    return exe, d
+
+
+@pytest.mark.parametrize("how", ["", "cta", "ops_cta"])
+def test_shared_memory_traffic_is_ordered(emu_tsan, how):
+    """Under ThreadSanitizer every read of a slot another lane or warp wrote
+    (plans, flat-step descriptors and keys, the CTA's reduction words) must
+    be ordered by the warp or CTA barrier the device code places; an
+    unordered one is reported as a race."""
+    exe, d = emu_tsan
+    rng = np.random.default_rng(3)
+    db = mixed_db(rng, 60, [2100], extra=(0, 2))
+    q = synth.residues(rng, 50)
+    p = O.paper_params()
+    hdr = struct.pack("<qqiiiiiiiIIIQq", db.n, len(db.codes), len(q), 2, p.pgp, p.gop, p.gep, p.rounds, p.mode,
+                      p.lfactor_q16, p.sfactor_q16, p.minfactor_q16, 1, 0)
+    inp, out = str(d / "in.bin"), str(d / "out.bin")
+    with open(inp, "wb") as f:
+        f.write(hdr)
+        f.write(O.blosum62().tobytes())
+        f.write(np.ascontiguousarray(db.codes, np.uint8).tobytes())
+        f.write(np.ascontiguousarray(db.offsets, np.int64).tobytes())
+        f.write(np.ascontiguousarray(q, np.uint8).tobytes())
+    r = subprocess.run([exe, inp, out] + ([how] if how else []), capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert "WARNING: ThreadSanitizer" not in r.stderr, r.stderr[:4000]
