@@ -271,3 +271,22 @@ def test_shared_memory_traffic_is_ordered(emu_tsan, how):
     r = subprocess.run([exe, inp, out] + ([how] if how else []), capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-3000:]
     assert "WARNING: ThreadSanitizer" not in r.stderr, r.stderr[:4000]
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_configurations(emu, case):
+    """Seeded random databases, queries, matrices and parameters: lengths
+    around the role switch and the one-per-warp threshold, matrix ranges
+    from 1 to 255, every factor and penalty in its accepted range."""
+    rng = np.random.default_rng(1000 + case)
+    qlen = int(rng.choice([1, 2, 5, 31, 64, 129, 256, 511, 1000]))
+    lengths = np.concatenate([rng.integers(0, 2 * qlen + 8, 40), [qlen - 1, qlen, qlen + 1],
+                              rng.integers(2000, 2200, int(rng.integers(0, 3)))]).clip(0)
+    db = synth.db_from_lengths(rng, lengths)
+    lo = int(rng.integers(-128, 0))
+    hi = int(rng.integers(lo + 1, 128))
+    M = synth.random_symmetric_matrix(rng, lo, hi)
+    p = O.paper_params(pgp=int(rng.integers(0, 6)), gop=int(rng.integers(0, 20)), gep=int(rng.integers(0, 8)),
+                       rounds=int(rng.integers(1, 4)), lfactor_q16=int(rng.integers(0, 65537)),
+                       sfactor_q16=int(rng.integers(0, 65537)), minfactor_q16=int(rng.integers(0, 65537)))
+    check(emu, db, synth.residues(rng, qlen), M, p, int(rng.integers(0, 2**63)), warps=int(rng.integers(1, 4)))
