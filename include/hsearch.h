@@ -248,8 +248,8 @@ int hs_search_batch(hs_db *db, int32_t nq, const uint8_t *queries, const int64_t
                     void *stream, hs_hit *hits_out, int32_t *n_hits_out, uint32_t *ops_out,
                     int64_t ops_cap, int64_t *ops_used);
 
-/* Threshold reporting (Sec. IV: hits "with appropriately set threshold
- * score").  The same search as hs_search, keeping every pair that scores
+/* Threshold reporting (Sec. IV reports the hits above a chosen threshold
+ * score).  The same search as hs_search, keeping every pair that scores
  * >= threshold, ranked, at most max_hits (<= HS_MAX_K) of them with their
  * alignments.  *n_above_out receives the number of pairs at or above the
  * threshold (more than *n_hits_out when max_hits truncated the list). */

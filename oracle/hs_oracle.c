@@ -33,7 +33,7 @@
  *   A4  lf = max(MinFactor, LFactor*U1), sf = max(MinFactor, SFactor*U2).
  *   A6  Q16 fixed point, floors; ls >= 1; 1 <= ss <= min(Srem, ls).
  *   A8  sub-sequences are prefixes of what is left of each sequence.
- *   A9  the used-up part of large is its first k*+ss letters.
+ *   A9  a step consumes the first k*+ss letters of large.
  *   A10 ties: lowest shift, first round.
  *   A12 random(): Philox4x64-10 draws, 16 bits each (see draw16 below).
  *   A13 large = target when |T| >= |Q|.
@@ -300,7 +300,7 @@ static int64_t align_round(const uint8_t *large, int64_t nl, const uint8_t *smal
                            uint8_t *rl, uint8_t *rs, int64_t *ncols_out, int64_t *cells)
 {
     int64_t Lp = 0, Sp = 0, t = 0, nc = 0;
-    while (Lp < nl && Sp < ns) {              /* "large is not empty AND small is not empty" */
+    while (Lp < nl && Sp < ns) {              /* until either sequence is used up (Fig. 1) */
         int64_t Lrem = nl - Lp, Srem = ns - Sp;
         /* ls = length(large) * LF, ss = length(small) * SF * random()  (A6) */
         int64_t ls = (int64_t)(((uint64_t)Lrem * lf) >> 16);
@@ -330,10 +330,10 @@ static int64_t align_round(const uint8_t *large, int64_t nl, const uint8_t *smal
         for (int64_t i = 0; i < kstar; i++) { rl[nc] = large[Lp + i]; rs[nc] = OR_GAP; nc++; }
         for (int64_t j = 0; j < ss; j++) { rl[nc] = large[Lp + kstar + j]; rs[nc] = small[Sp + j]; nc++; }
         Lp += kstar + ss;
-        Sp += ss;                             /* "delete from small the first ss letters" */
+        Sp += ss;                             /* small gives up its first ss letters (A9) */
         t++;
     }
-    /* "append the remaining with dashes to align" */
+    /* the leftover letters of either sequence go against gaps (Fig. 1) */
     while (Lp < nl) { rl[nc] = large[Lp++]; rs[nc] = OR_GAP; nc++; }
     while (Sp < ns) { rl[nc] = OR_GAP; rs[nc] = small[Sp++]; nc++; }
     *ncols_out = nc;
@@ -435,7 +435,7 @@ int32_t or_search_scores(const uint8_t *codes, const int64_t *offsets, const int
     return started + 1;
 }
 
-/* Ranking (Sec. IV "threshold score", read as top-k): order by score
+/* Ranking (Sec. IV's threshold reporting, read as top-k): order by score
  * descending, then database index ascending (A10).  Plain selection of
  * the k best by repeated scans -- O(n k), fine for an oracle. */
 int32_t or_topk(const int64_t *scores, int64_t n, int32_t k, int64_t *idx_out)

@@ -756,7 +756,7 @@ __device__ __forceinline__ int32_t align_round_full(const PairCtx &c, const SPar
         Sp += ss;
         t++;
     }
-    // "append the remaining with dashes": large's rest against gaps in small's row, or small's rest
+    // the end of Align (Fig. 1): large's rest against gaps in small's row, or small's rest
     rs.gap(1, nl - Lp);
     rs.gap(0, ns - Sp);
     rs.finish(kp);

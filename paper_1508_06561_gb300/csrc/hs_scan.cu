@@ -112,8 +112,8 @@ __device__ __forceinline__ void lane_start_round(Lane &L, const SParams &sp)
     L.Lp = 0; L.Sp = 0; L.step = 0; L.score = 0;
 }
 
-// Finish every round whose loop has ended (Fig. 1: "append the remaining
-// with dashes"; AlignSequences keeps the first best round), then the pair.
+// Finish every round whose loop has ended (Fig. 1: the leftover letters go
+// against gaps; AlignSequences keeps the first best round), then the pair.
 __device__ __forceinline__ void lane_settle(Lane &L, const SParams &sp, const QueryCtx &qc)
 {
     while (L.d >= 0 && !(L.Lp < L.nl && L.Sp < L.ns)) {
@@ -307,7 +307,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             coop_scan_t<P16>(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
             if (lane == i) { vmax = v; kstar = k; }
         }
-        // consume (Fig. 1: delete the used-up parts) and score incrementally (A17)
+        // consume (Fig. 1: drop what the step took from both) and score incrementally (A17)
         if (busy) {
             L.cells += (int64_t)(g.ls - g.ss + 1) * g.ss;
             int32_t gap = 0;
