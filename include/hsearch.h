@@ -160,6 +160,9 @@ int64_t hs_ops_capacity(int32_t qlen, int32_t k);
  *   d_cells     : optional device int64[n_seqs], the virtual-score cells
  *                 (letter pairs summed) of every pair (NULL: not counted).
  *   d_status    : device int32 receiving HS_OK or the first device-side error.
+ *                 A letter code >= 24 in d_query (which the host cannot
+ *                 see) is reported here as HS_EINVAL; that column scores 0
+ *                 and no memory outside the buffers is read.
  * Host-side argument errors are returned before anything is enqueued. */
 int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen,
                      const hs_params *p, int32_t k, uint64_t seed, void *stream,
@@ -182,7 +185,10 @@ int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen,
  *     query and k = 100).
  *   - Set-up: the first call on each device looks up the array's device
  *     address (cudaGetSymbolAddress) with that device current; make that
- *     first call before any stream capture.
+ *     first call before any stream capture.  After a device reset the first
+ *     call on the new context looks it up again (the old address is gone).
+ *   - Query codes: as for hs_search_device, a code >= 24 in d_query is
+ *     reported as HS_EINVAL in *d_status.
  *   - Sharing: all calls on a device use the same array, which keeps the last
  *     call's contents; each call clears what must start at zero.  Calls
  *     whose work overlaps on the GPU (other streams, other threads) race on
@@ -232,7 +238,8 @@ int64_t hs_batch_ops_capacity(int32_t nq, int64_t total_qlen, int32_t k);
  * no allocation, so it can be captured in a CUDA graph by the caller).
  *   d_queries, d_qoffsets (int64[nq+1]), d_seeds (uint64[nq]): device; the
  *   offsets must describe queries of 1..max_qlen letters totalling
- *   total_qlen (the host cannot check device data).
+ *   total_qlen (the host cannot check device data); letter codes >= 24 are
+ *   reported as HS_EINVAL in *d_status.
  *   d_hits: nq*k records; d_ops/ops_cap/d_ops_used/d_status as for
  *   hs_search_device. */
 int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries, const int64_t *d_qoffsets,

@@ -414,8 +414,8 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
     int launches = 0;
     {
         NvtxRange r("hs.scan");
-        e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, db->num_sms, st, db->trace ? &tr : nullptr,
-                        &launches, input_order);
+        e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, d_status, db->num_sms, st,
+                        db->trace ? &tr : nullptr, &launches, input_order);
         if (e == cudaSuccess && d_count)
             e = launch_count_at_least(ws.scores, db->n, min_score, d_count, db->num_sms, st, &launches);
     }
@@ -686,7 +686,7 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     e = launch_prof_offsets(bl, st);
     launches++;
     if (e == cudaSuccess)
-        e = launch_scan_batch(v, db->d_cumres, long_end, kp, bl, nchunk, ctas_per_sm, db->num_sms, st,
+        e = launch_scan_batch(v, db->d_cumres, long_end, kp, bl, nchunk, ctas_per_sm, db->num_sms, d_status, st,
                               db->trace ? &tr : nullptr, &launches, db->schedule == HS_SCHEDULE_INPUT);
     if (e == cudaSuccess && nhits > 0) e = launch_topk_batch(bl, db->n, k, nhits, st, &launches);
     if (e == cudaSuccess && nhits > 0)

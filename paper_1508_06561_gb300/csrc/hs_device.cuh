@@ -80,7 +80,7 @@ __device__ __forceinline__ uint32_t profile_word_value(const uint8_t *q, int qle
         uint32_t v = 0;
         if (c >= 0 && c < qlen) {
             const int qc = q[rev ? qlen - 1 - c : c];
-            v = (uint32_t)(m[qc * kNSym + a] + bias) & 0xFFu;
+            if (qc < kNSym) v = (uint32_t)(m[qc * kNSym + a] + bias) & 0xFFu;   // bad codes: see profile_kernel
         }
         word |= v << (8 * b);
     }

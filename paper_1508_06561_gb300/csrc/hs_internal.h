@@ -111,7 +111,7 @@ struct ScanTrace {
     cudaEvent_t start, stop;
 };
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
-                        const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
+                        const KParams &kp, const Workspace &ws, int64_t *d_cells, int32_t *d_status, int num_sms,
                         cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order);
 size_t scan_smem_bytes(int32_t qlen);
 cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches);
@@ -120,7 +120,8 @@ cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32
 cudaError_t launch_prof_offsets(const BatchLayout &bl, cudaStream_t st);
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
                               const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
-                              cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order);
+                              int32_t *d_status, cudaStream_t st, const ScanTrace *trace, int *launches,
+                              bool input_order);
 cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const BatchLayout &bl, int32_t nhits,
                                 int32_t k, hs_hit *d_hits, uint32_t *d_ops, int64_t ops_cap, int64_t *d_ops_used,
                                 int32_t *d_status, cudaStream_t st, int *launches);

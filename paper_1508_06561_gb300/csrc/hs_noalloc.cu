@@ -23,19 +23,45 @@ static __device__ __align__(256) unsigned char g_scratch[HS_NOALLOC_SCRATCH_BYTE
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices];
+void *g_scratch_ctx[kMaxDevices];       // the context the cached address belongs to
+
+// The current context, through the driver's cuCtxGetCurrent (found once via
+// the runtime, so the library links no driver library).  nullptr if unknown.
+void *current_context()
+{
+    typedef int (*CtxGetCurrent)(void **);
+    static CtxGetCurrent fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrent>(f);
+    }();
+    void *ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 // Device address of g_scratch on the current device.  Host code only has a
-// host-side stand-in for the array, so the address is looked up once per
-// device with cudaGetSymbolAddress, with that device current, and cached.
+// host-side stand-in for the array, so the address is looked up with
+// cudaGetSymbolAddress, with the device current, once per device and
+// context: a device reset (cudaDeviceReset, or the primary context torn down
+// and made again) reloads the library's device image at a new address, and
+// the first call after it looks the address up again.  Where the context
+// cannot be read, the address is looked up on every call (the lookup
+// allocates nothing).
 int scratch_address(void **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HS_ECUDA;
+    void *ctx = current_context();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HS_ECUDA;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return HS_OK;

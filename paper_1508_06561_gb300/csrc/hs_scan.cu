@@ -22,6 +22,7 @@ struct ProfileJob {
     const int64_t *prof_off;      // word offset of each query's profiles (batched)
     int32_t qlen;
     uint32_t *prof;
+    int32_t *status;              // HS_EINVAL is recorded here for a letter code >= kNSym
 };
 
 __global__ void profile_kernel(ProfileJob job, KParams kp)
@@ -38,6 +39,11 @@ __global__ void profile_kernel(ProfileJob job, KParams kp)
         qlen = (int)(job.qoffsets[qi + 1] - job.qoffsets[qi]);
         prof += job.prof_off[qi];
     }
+    // Device-resident queries reach the library unchecked: a code outside the
+    // alphabet is reported through the status word and scores as a zero
+    // column (profile_word_value) instead of indexing past the matrix.
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < qlen; i += gridDim.x * blockDim.x)
+        if (q[i] >= kNSym && job.status) atomicCAS(job.status, (int32_t)HS_OK, (int32_t)HS_EINVAL);
     const int R = profile_stride(qlen);
     const int64_t words = profile_words(qlen);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * words;
@@ -512,11 +518,11 @@ size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
 static bool fuse_roles(int32_t qlen) { return 2 * scan_smem_bytes(qlen) <= 100 * 1024; }
 
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
-                        const KParams &kp, const Workspace &ws, int64_t *d_cells, int num_sms,
+                        const KParams &kp, const Workspace &ws, int64_t *d_cells, int32_t *d_status, int num_sms,
                         cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order)
 {
     const int64_t words = profile_words(kp.s.qlen);
-    ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof};
+    ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof, d_status};
     profile_kernel<<<64, 256, 0, st>>>(job, kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -759,9 +765,10 @@ __global__ void batch_classes_kernel(const int64_t *qoffsets, int32_t nq, int32_
 
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
                               const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
-                              cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order)
+                              int32_t *d_status, cudaStream_t st, const ScanTrace *trace, int *launches,
+                              bool input_order)
 {
-    ProfileJob job = {bl.queries, bl.qoffsets, bl.prof_off, 0, bl.prof};
+    ProfileJob job = {bl.queries, bl.qoffsets, bl.prof_off, 0, bl.prof, d_status};
     profile_kernel<<<dim3(16, bl.nq), 256, 0, st>>>(job, kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1042,7 +1049,7 @@ cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KP
                               const Workspace &ws, int64_t db_index, uint32_t *d_ops, int64_t cap,
                               hs_hit *d_hit, int64_t *d_ops_used, int32_t *d_status, cudaStream_t st)
 {
-    ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof};
+    ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof, d_status};
     profile_kernel<<<64, 256, 0, st>>>(job, kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -78,6 +78,9 @@ class Server:
     def __init__(self, db: Database, k: int = 100, params: Params | None = None, max_batch: int = 64,
                  slots: int = 2, max_qlen: int = 2048, max_total_qlen: int = 32768, tuning=None, device=None):
         import torch
+        if max_total_qlen < max_qlen:
+            raise ValueError("max_total_qlen (%d) must be at least max_qlen (%d): a request of max_qlen letters "
+                             "must fit a batch alone" % (max_total_qlen, max_qlen))
         self.db, self.k, self.params = db, k, params or Params()
         self.max_batch, self.max_qlen, self.max_total = max_batch, max_qlen, max_total_qlen
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -97,8 +100,10 @@ class Server:
     # ------------------------------------------------------------------
     def submit(self, query, seed: int = 0) -> Future:
         q = np.asarray(query)
-        if len(q) < 1 or len(q) > self.max_qlen:
+        if q.ndim != 1 or len(q) < 1 or len(q) > self.max_qlen:
             raise ValueError("query length must be in [1, %d]" % self.max_qlen)
+        if q.dtype.kind not in "ui" or int(q.min()) < 0 or int(q.max()) >= 24:
+            raise ValueError("query letters must be alphabet codes 0..23 (see encode())")
         r = _Req(q, seed)
         with self.cv:
             self.queue.append(r)
@@ -133,7 +138,15 @@ class Server:
                     continue
                 L = len(r.query)
                 if not self._fits(len(batch) + 1, total + L, max(mq, L)):
-                    break
+                    if batch:
+                        break
+                    # it does not fit even alone: fail it rather than stall the queue
+                    self.queue.popleft()
+                    if r.future.set_running_or_notify_cancel():
+                        r.future.set_exception(ValueError("request does not fit one slot's device memory"))
+                    else:
+                        self.cancelled += 1
+                    continue
                 self.queue.popleft()
                 if not r.future.set_running_or_notify_cancel():     # cancelled just now
                     self.cancelled += 1
@@ -183,9 +196,20 @@ class Server:
         self.batches.append((nq, total))
 
     def _harvest(self, s: _Slot):
-        import torch
-        batch, nq, nh = s.batch
+        batch = s.batch[0]
         s.batch = None
+        try:
+            self._deliver(s, batch)
+        except Exception as e:
+            # every caller of the batch learns of the failure; none waits forever
+            self.errors.append(e)
+            for r in batch:
+                if not r.future.done():
+                    r.future.set_exception(e)
+
+    def _deliver(self, s: _Slot, batch):
+        import torch
+        nq, nh = len(batch), min(self.k, self.db.n)
         used = int(s.h_meta[0].item())
         status = int(s.h_meta[1].item()) & 0xFFFFFFFF
         if status != 0:
@@ -220,10 +244,7 @@ class Server:
             progressed = False
             for s in self.slots:
                 if s.batch is not None and s.event.query():
-                    try:
-                        self._harvest(s)
-                    except Exception as e:          # pragma: no cover - reported to the callers
-                        self.errors.append(e)
+                    self._harvest(s)
                     progressed = True
             for s in self.slots:
                 if s.batch is None:

@@ -115,3 +115,34 @@ def test_small_workspace_is_rejected_before_launch(small_db):
     assert call(need) == 0
     torch.cuda.synchronize()
     assert int(meta[1].item()) & 0xFFFFFFFF == 0
+
+
+def test_bad_letter_codes_on_device_report_einval(small_db):
+    """A device-resident query holding a code outside the 24-letter alphabet
+    (the host cannot look at it) comes back as HS_EINVAL in the status word
+    of every device entry point, reads nothing out of range, and leaves the
+    context usable: the next search of a good query equals the host search."""
+    db, D = small_db
+    rng = np.random.default_rng(9)
+    good = synth.residues(rng, 40)
+    for bad_code in (24, 65, 255):
+        q = good.copy()
+        q[17] = bad_code
+        qd = torch.from_numpy(q).cuda()
+        out = P.search_device(D, qd, 5)
+        torch.cuda.synchronize()
+        assert int(out["status"].item()) == HS_EINVAL
+        P.search_device_noalloc(D, qd, 5, out)
+        torch.cuda.synchronize()
+        assert int(out["status"].item()) == HS_EINVAL
+        cat = torch.from_numpy(np.concatenate([good, q])).cuda()
+        off = torch.tensor([0, len(good), 2 * len(good)], dtype=torch.int64, device="cuda")
+        seeds = torch.zeros(2, dtype=torch.int64, device="cuda")
+        bo = P.search_batch_device(D, cat, off, seeds, len(good), 5)
+        torch.cuda.synchronize()
+        assert int(bo["status"].item()) == HS_EINVAL
+    out = P.search_device(D, torch.from_numpy(good).cuda(), 5)
+    torch.cuda.synchronize()
+    hits, ops = P.device_result_to_host(out)
+    hh, ho = P.search(D, good, 5)
+    assert np.array_equal(hits, hh) and np.array_equal(ops, ho)

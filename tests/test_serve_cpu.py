@@ -49,3 +49,60 @@ def test_latency_stats():
     st = serve.latency_stats([0.001 * i for i in range(1, 101)])
     assert abs(st["p50_ms"] - 50.5) < 1e-9 and abs(st["p99_ms"] - 99.01) < 1e-6
     assert serve.latency_stats([])["p50_ms"] is None
+
+
+def test_a_request_that_never_fits_fails_instead_of_stalling_the_queue():
+    srv = fake_server(lambda nq, total, mq: total <= 50)
+    reqs = [serve._Req(np.zeros(L, np.uint8), i) for i, L in enumerate([60, 30, 5])]
+    srv.queue.extend(reqs)
+    batch, total, _ = srv._admit()
+    assert [r.seed for r in batch] == [1, 2] and total == 35
+    assert isinstance(reqs[0].future.exception(timeout=0), ValueError)
+    assert not srv.queue
+
+
+def test_a_failed_harvest_resolves_every_future_of_the_batch():
+    """An error while results are copied out reaches every caller of the
+    batch (as its exception) and the server's error list."""
+    srv = serve.Server.__new__(serve.Server)
+    srv.errors = []
+
+    class Boom(RuntimeError):
+        pass
+
+    def deliver(slot, batch):
+        batch[0].future.set_result("first one done")
+        raise Boom("copy failed")
+
+    srv._deliver = deliver
+    slot = type("S", (), {})()
+    reqs = [serve._Req(np.zeros(4, np.uint8), i) for i in range(3)]
+    for r in reqs:
+        r.future.set_running_or_notify_cancel()
+    slot.batch = (reqs, 3, 3)
+    srv._harvest(slot)
+    assert slot.batch is None
+    assert reqs[0].future.result(timeout=0) == "first one done"
+    for r in reqs[1:]:
+        assert isinstance(r.future.exception(timeout=0), Boom)
+    assert len(srv.errors) == 1
+
+
+def test_submit_rejects_codes_outside_the_alphabet():
+    srv = fake_server(lambda nq, total, mq: True)
+    srv.max_qlen = 100
+    import pytest
+    with pytest.raises(ValueError):
+        srv.submit(np.array([1, 2, 24], np.uint8))
+    with pytest.raises(ValueError):
+        srv.submit(np.array([65, 66], np.uint8))
+    with pytest.raises(ValueError):
+        srv.submit(np.zeros(101, np.uint8))
+    f = srv.submit(np.array([0, 23], np.uint8))
+    assert not f.done() and len(srv.queue) == 1
+
+
+def test_slot_budget_below_the_longest_request_is_refused():
+    import pytest
+    with pytest.raises(ValueError):
+        serve.Server(None, max_qlen=2048, max_total_qlen=1000)
