@@ -7,9 +7,11 @@ share no code: the oracle has its own alphabet, matrix parser, Philox generator
 and algorithm, all in ``hs_oracle.c`` (plain C, compiled with gcc by
 ``build()``), following Fig. 1 and Sec. III.B of the paper step by step.
 
-Parity of the heuristic's own choices (which shift wins, how long each piece
-is) is unpinned beyond the invariants the tests check (rescore, DP optimum
-bound, self-alignment closed form); the GPU path must agree with it bit for bit.
+The heuristic's own choices (how long each piece is, which shift wins, what
+each step lays out) are pinned by an independent step trace in the tests
+(numpy's Philox, integer piece sizes, numpy sliding-window argmax), beside
+the invariants (rescore, DP optimum bound, closed forms); the GPU path must
+agree with the oracle bit for bit.
 """
 from __future__ import annotations
 
@@ -63,35 +65,41 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        P = C.POINTER
-        u8p, i8p, i64p, u64p, i32p = P(C.c_uint8), P(C.c_int8), P(C.c_int64), P(C.c_uint64), P(C.c_int32)
-        L.or_philox4x64_10.argtypes = [u64p, u64p, u64p]
-        L.or_draw16.argtypes = [C.c_uint64] * 4
-        L.or_draw16.restype = C.c_uint32
-        L.or_encode.argtypes = [C.c_char_p, C.c_int64, u8p]
-        L.or_parse_matrix.argtypes = [C.c_char_p, i8p]
-        L.or_parse_matrix.restype = C.c_int
-        L.or_score_rows.argtypes = [u8p, u8p, C.c_int64, i8p, C.c_int32, C.c_int32, C.c_int32, i64p]
-        L.or_score_rows.restype = C.c_int
-        L.or_best_shift.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, i64p]
-        L.or_best_shift.restype = C.c_int64
-        L.or_best_shift_full.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, i64p]
-        L.or_best_shift_full.restype = C.c_int64
-        L.or_align_pair.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, P(Params), C.c_uint64,
-                                    C.c_uint64, u8p, u8p, i64p, i32p, i64p]
-        L.or_align_pair.restype = C.c_int64
-        L.or_search_scores.argtypes = [u8p, i64p, i64p, C.c_int64, u8p, C.c_int64, i8p, P(Params),
-                                       C.c_uint64, C.c_int32, i64p, i64p]
-        L.or_search_scores.restype = C.c_int32
-        L.or_topk.argtypes = [i64p, C.c_int64, C.c_int32, i64p]
-        L.or_topk.restype = C.c_int32
-        L.or_periphery_opt.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, C.c_int32, C.c_int32, C.c_int32]
-        L.or_periphery_opt.restype = C.c_int64
-        L.or_smith_waterman.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, C.c_int32, C.c_int32]
-        L.or_smith_waterman.restype = C.c_int64
-        _lib = L
+        _lib = load(build())
     return _lib
+
+
+def load(path):
+    """Loads a build of hs_oracle.c with the argument types declared (the
+    tests also load copies with planted mistakes, to show the pins catch them)."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    u8p, i8p, i64p, u64p, i32p = P(C.c_uint8), P(C.c_int8), P(C.c_int64), P(C.c_uint64), P(C.c_int32)
+    L.or_philox4x64_10.argtypes = [u64p, u64p, u64p]
+    L.or_draw16.argtypes = [C.c_uint64] * 4
+    L.or_draw16.restype = C.c_uint32
+    L.or_encode.argtypes = [C.c_char_p, C.c_int64, u8p]
+    L.or_parse_matrix.argtypes = [C.c_char_p, i8p]
+    L.or_parse_matrix.restype = C.c_int
+    L.or_score_rows.argtypes = [u8p, u8p, C.c_int64, i8p, C.c_int32, C.c_int32, C.c_int32, i64p]
+    L.or_score_rows.restype = C.c_int
+    L.or_best_shift.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, i64p]
+    L.or_best_shift.restype = C.c_int64
+    L.or_best_shift_full.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, i64p]
+    L.or_best_shift_full.restype = C.c_int64
+    L.or_align_pair.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, P(Params), C.c_uint64,
+                                C.c_uint64, u8p, u8p, i64p, i32p, i64p]
+    L.or_align_pair.restype = C.c_int64
+    L.or_search_scores.argtypes = [u8p, i64p, i64p, C.c_int64, u8p, C.c_int64, i8p, P(Params),
+                                   C.c_uint64, C.c_int32, i64p, i64p]
+    L.or_search_scores.restype = C.c_int32
+    L.or_topk.argtypes = [i64p, C.c_int64, C.c_int32, i64p]
+    L.or_topk.restype = C.c_int32
+    L.or_periphery_opt.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, C.c_int32, C.c_int32, C.c_int32]
+    L.or_periphery_opt.restype = C.c_int64
+    L.or_smith_waterman.argtypes = [u8p, C.c_int64, u8p, C.c_int64, i8p, C.c_int32, C.c_int32]
+    L.or_smith_waterman.restype = C.c_int64
+    return L
 
 
 def _p(a, t):
@@ -168,8 +176,9 @@ def best_shift_full(large, small, M):
     return int(k.value), int(v)
 
 
-def align_pair(q, t, M, params: Params, seed: int, dbidx: int):
-    """AlignSequences for one pair: (score, query_row, target_row, round, cells)."""
+def align_pair(q, t, M, params: Params, seed: int, dbidx: int, using=None):
+    """AlignSequences for one pair: (score, query_row, target_row, round, cells).
+    using: another loaded build (load()) instead of this one."""
     q, t, M = _u8(q), _u8(t), _mat(M)
     cap = len(q) + len(t) + 1
     rq = np.zeros(cap, np.uint8)
@@ -177,7 +186,7 @@ def align_pair(q, t, M, params: Params, seed: int, dbidx: int):
     n = C.c_int64()
     r = C.c_int32()
     cells = C.c_int64()
-    s = lib().or_align_pair(_p(q, C.c_uint8), len(q), _p(t, C.c_uint8), len(t), _p(M, C.c_int8),
+    s = (using or lib()).or_align_pair(_p(q, C.c_uint8), len(q), _p(t, C.c_uint8), len(t), _p(M, C.c_int8),
                             C.byref(params), seed, dbidx, _p(rq, C.c_uint8), _p(rt, C.c_uint8),
                             C.byref(n), C.byref(r), C.byref(cells))
     return int(s), rq[:n.value].copy(), rt[:n.value].copy(), int(r.value), int(cells.value)

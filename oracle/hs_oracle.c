@@ -10,11 +10,15 @@
  * code, table or header with it: this file has its own alphabet table, its
  * own matrix parser and its own Philox generator.
  *
- * Parity unpinned for the heuristic's own choices (which shift wins, how
- * long each piece is): nothing outside the paper's algorithm fixes them, so
- * the tests pin only what the mathematics does -- Philox known answers,
- * SCORE closed forms, the exact DP optimum as an upper bound, rescoring of
- * the emitted rows, sliding-window argmax, special cases with closed forms.
+ * The heuristic's own choices (how long each piece is, which shift wins,
+ * what a step lays out) are pinned by an independent step trace in the
+ * tests: draws sliced from numpy's Philox, the piece sizes in Python
+ * integers, the best shift by a numpy sliding-window argmax; it predicts
+ * every alignment column and the cell count, and copies of this file with
+ * plausible mistakes planted fail it.  The rest is pinned by what the
+ * mathematics fixes -- Philox known answers, SCORE closed forms, the exact
+ * DP optimum as an upper bound, rescoring of the emitted rows, special cases
+ * with closed forms.
  *
  * Structure follows Fig. 1 of the paper:
  *   or_align_sequences   -- AlignSequences: best of `rounds` randomised runs
@@ -54,9 +58,9 @@
  * published known-answer vectors; SCORE against closed forms; the
  * periphery DP against exhaustive enumeration and against Smith-Waterman
  * (PGP = 0); the heuristic against the DP optimum, the rescore of its own
- * rows and the self-alignment closed form.  The heuristic's own choices
- * (which shift, which sizes) have no external reference: beyond those
- * invariants their parity is unpinned, and GPU/oracle agreement is the check.
+ * rows, the self-alignment closed form, and step by step (piece sizes,
+ * shifts, the rows of both modes, cell counts) against the independent
+ * trace of tests/test_oracle_steps.py, a hand-worked first step included.
  */
 #include <stdint.h>
 #include <stdlib.h>
