@@ -43,3 +43,33 @@ def test_schedules_agree():
     for (h0, _), (hb, _) in zip(a[0], a[1]):
         assert np.array_equal(h0, hb)
     D.close()
+
+
+@pytest.mark.slow
+def test_load_balance_workload_matches_oracle_under_both_schedules():
+    """The load-balance workload itself (100k targets, 90% of 50-150 letters
+    and 10% of 5,000-35,000; 16 queries of 50, 500 and 2,000 letters; top
+    50): under the length-binned schedule and in database order, every
+    pair's score and cell count, the ranked hits and every hit's alignment
+    equal the oracle's, for the plain searches and for the batched search of
+    all 16 queries (Sec. III.B.3 search, Fig. 1 per pair)."""
+    import oracle as O
+    from gpu_checks import check_hits, run_device
+    O.build()
+    db, qs, k = synth.bimodal()
+    D = P.Database(db.codes, db.offsets)
+    M, op = O.blosum62(), O.paper_params()
+    seeds = [1000 + i for i in range(len(qs))]
+    refs = [O.search_scores(db.codes, db.offsets, q, M, op, s) for q, s in zip(qs, seeds)]
+    for sched in (P.Database.SCHEDULE_LENGTH, P.Database.SCHEDULE_INPUT):
+        D.set_schedule(sched)
+        batch = P.search_batch(D, qs, k, seeds=seeds)
+        for i, (q, s) in enumerate(zip(qs, seeds)):
+            ref, ref_cells, _ = refs[i]
+            hits, ops, scores, cells = run_device(D, q, k, P.Params(), s)
+            bad = np.nonzero(scores != ref)[0]
+            assert len(bad) == 0, "schedule %d query %d: score mismatch at %s" % (sched, i, bad[:5])
+            assert np.array_equal(cells, ref_cells)
+            check_hits(db, q, M, op, s, hits, ops, ref, k)
+            check_hits(db, q, M, op, s, batch[i][0], batch[i][1], ref, k)
+    D.close()

@@ -96,3 +96,53 @@ def test_cancelled_requests_do_not_disturb_the_rest(db):
     for i in list(done)[::7]:
         h0, o0 = P.search(db, qs[i], 5, seed=100 + i)
         assert np.array_equal(done[i][0], h0) and np.array_equal(done[i][1], o0)
+
+
+@pytest.mark.slow
+def test_served_requests_match_oracle_on_the_570k_database():
+    """The serving workload's stream (Poisson arrivals, query lengths
+    lognormal with median 250 clamped to [20, 2000], a seed per request)
+    against the resident ~570k-sequence database, top 100, at 200 and
+    1,000 requests/s: 500 requests per rate.  Every served hit's score,
+    alignment rows and core span equal the oracle's alignment of that pair
+    (Fig. 1), hits come ranked by (score desc, index asc), and for 10
+    requests per rate the oracle scores the whole database and the served
+    top 100 is its ranking (Sec. III.B.3)."""
+    import oracle as O
+    from gpu_checks import check_hits
+    O.build()
+    dbh, _, k = synth.plain_large()
+    D = P.Database(dbh.codes, dbh.offsets)
+    M, op = O.blosum62(), O.paper_params()
+    params = P.Params()
+    try:
+        for rate in (200.0, 1000.0):
+            t_arr, qs, seeds = synth.serving_stream(5, 500, rate)
+            srv = serve.Server(D, k=k, params=params, max_batch=64, slots=3, max_total_qlen=65536)
+            futs = []
+            t0 = time.perf_counter()
+            for ta, q, sd in zip(t_arr, qs, seeds):
+                delay = t0 + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                futs.append(srv.submit(q, int(sd)))
+            res = [f.result(timeout=600) for f in futs]
+            srv.close()
+            assert not srv.errors
+            if rate == 1000.0:
+                assert max(nq for nq, _ in srv.batches) > 1          # requests were batched together
+            for i, (h, o) in enumerate(res):
+                q, sd = qs[i], int(seeds[i])
+                assert len(h) == k
+                key = [(-int(x["score"]), int(x["db_index"])) for x in h]
+                assert key == sorted(key)
+                for x in h:
+                    t = dbh.seq(int(x["db_index"]))
+                    rq, rt = P.ops_to_rows(o[x["ops_offset"]:x["ops_offset"] + x["ops_len"]], q, t)
+                    s, oq, ot, _, _ = O.align_pair(q, t, M, op, sd, int(x["db_index"]))
+                    assert s == x["score"] and np.array_equal(rq, oq) and np.array_equal(rt, ot)
+            for i in np.linspace(0, len(qs) - 1, 10).astype(int):
+                ref, _, _ = O.search_scores(dbh.codes, dbh.offsets, qs[i], M, op, int(seeds[i]), want_cells=False)
+                check_hits(dbh, qs[i], M, op, int(seeds[i]), res[i][0], res[i][1], ref, k)
+    finally:
+        D.close()
