@@ -51,9 +51,13 @@ def parse_args():
                     help="wall-time budget of the oracle CPU baseline sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per serving rate (max)")
-    ap.add_argument("--bimodal", action="store_true",
-                    help="also time the load-balance workload under both schedules")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="offered seconds of traffic per serving rate (requests = rate x this, at most 10,000)")
+    ap.add_argument("--no-bimodal", action="store_true",
+                    help="skip the load-balance workload (both schedules)")
+    ap.add_argument("--no-small", action="store_true", help="skip the plain-small workload section")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the integer issue-rate measurement (the roofline then uses the derived peak)")
     return ap.parse_args()
 
 
@@ -290,11 +294,12 @@ def batched_section(P, D, db, params, seed, reps=3):
 # median 250, clamped to [20, 2000], one seed each) against the resident
 # database, continuous batching; p50/p99 latency beside throughput
 # --------------------------------------------------------------------------
-def serving_section(P, D, db, params, max_requests, rates=(50.0, 200.0, 1000.0)):
+def serving_section(P, D, db, params, seconds, rates=(50.0, 200.0, 1000.0)):
     from paper_1508_06561_gb300 import serve, synth
-    out = {"workload": "serving-swissprot-like-570k", "k": 100, "rates": []}
+    out = {"workload": "serving-swissprot-like-570k", "k": 100, "rates": [],
+           "requests_note": "rate x %.0f s of offered traffic per rate, at most the stream's 10,000" % seconds}
     for rate in rates:
-        n = int(min(max_requests, max(50, rate * 4)))
+        n = int(min(10_000, max(50, rate * seconds)))
         t_arr, qs, seeds = synth.serving_stream(5, n, rate)
         srv = serve.Server(D, k=100, params=params, max_batch=64, slots=3, max_total_qlen=65536)
         futs = []
@@ -367,6 +372,83 @@ def bimodal_section(P):
 
 
 # --------------------------------------------------------------------------
+# integer issue rates (libhspeak.so): the denominators of the scan's roofline
+# --------------------------------------------------------------------------
+def int_peaks(dev, uuid):
+    import ctypes as C
+
+    from paper_1508_06561_gb300 import build
+    L = C.CDLL(build.PEAK_LIB)
+    L.hsp_measure.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    out = {"how": "libhspeak.so: 8 interleaved dependency chains per thread, 1024-thread blocks on every SM, "
+                  "best of 5 launches by CUDA events"}
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    for name, op, iters in (("iadd", 0, 20000), ("dpx_vimax3", 1, 8000), ("dpx_viaddmax", 2, 8000)):
+        rate, ms, ops = C.c_double(), C.c_double(), C.c_int64()
+        rc = L.hsp_measure(op, iters, 5, None, C.byref(rate), C.byref(ms), C.byref(ops))
+        if rc != 0:
+            raise RuntimeError("hsp_measure(%s) failed: %d" % (name, rc))
+        out[name] = {"tops": rate.value / 1e12, "ms": ms.value, "ops_per_launch": int(ops.value)}
+    out["clocks"] = clocks.stop()
+    return out
+
+
+# --------------------------------------------------------------------------
+# plain single query on the small database (64-residue query, 2,000 targets,
+# top-10): the whole database sits in L2, so steps run warm
+# --------------------------------------------------------------------------
+def small_section(P, params, seed, steps=2000):
+    import torch
+
+    from paper_1508_06561_gb300 import synth
+    db, q, k = synth.plain_small(0)
+    D = P.Database(db.codes, db.offsets)
+    st = torch.cuda.Stream()
+    qd = torch.from_numpy(q).cuda()
+    # a search here takes tens of microseconds on the device, less than one
+    # Python call: the device-side rate is timed by replaying a CUDA graph of
+    # `per_graph` searches (hs_search_device allocates nothing and never
+    # synchronises, so it can be captured)
+    per_graph = 50
+    with torch.cuda.stream(st):
+        out = P.search_device(D, qd, k, params, seed=seed, stream=st)
+        for _ in range(20):
+            P.search_device(D, qd, k, params, seed=seed, stream=st, workspace=out["workspace"], out=out)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        for _ in range(per_graph):
+            P.search_device(D, qd, k, params, seed=seed, stream=st, workspace=out["workspace"], out=out)
+    reps = max(1, steps // per_graph)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            g.replay()
+        b.record(st)
+    st.synchronize()
+    assert int(out["status"].item()) == 0
+    steps = reps * per_graph
+    t = a.elapsed_time(b) / 1000.0
+    n_e2e = 500
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        P.search(D, q, k, params, seed=seed, stream=st)
+    te = time.perf_counter() - t0
+    D.close()
+    return {"workload": "plain-q64-2k", "n_seqs": int(db.n), "residues": int(db.residues), "qlen": int(len(q)),
+            "k": int(k), "value": steps * db.residues / t, "unit": UNIT, "ms_per_search": t * 1000.0 / steps,
+            "timing": "CUDA graph of %d searches replayed %d times, CUDA events" % (per_graph, reps),
+            "e2e": {"value": n_e2e * db.residues / te, "unit": UNIT, "ms_per_search": te * 1000.0 / n_e2e},
+            "l2": "database fits in L2; steps run warm"}
+
+
+# --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
@@ -394,18 +476,30 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(dev)
     qd = torch.from_numpy(q).to(dev)
 
-    # one untimed search counts the algorithmic cells (the scan's work)
+    # one untimed search counts the algorithmic work: per pair, the cells
+    # (one add each) and the shifts (one compare each), packed by the trace hook
+    tr = _lib.hs_trace()
+    tr.pack_shifts = 1
+    L.hs_db_set_trace(D.handle, C.byref(tr))
     with torch.cuda.stream(stream):
         out = P.search_device(D, qd, k, params, seed=args.seed, stream=stream, want_cells=True)
     stream.synchronize()
-    cells_per_search = int(out["cells"][: D.n].sum().item())
+    packed = out["cells"][: D.n]
+    cells_per_search = int((packed & ((1 << 40) - 1)).sum().item())
+    shifts_per_search = int((packed >> 40).sum().item())
     assert int(out["status"].item()) == 0
+    tr.pack_shifts = 0
     out = P.search_device(D, qd, k, params, seed=args.seed, stream=stream)   # buffers without counters
     ws = out["workspace"]
 
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    peaks = int_peaks(dev, uuid) if (rank == 0 and not args.no_peaks) else None
+
     # trace hook: events around the scan kernel of every timed step
-    tr = _lib.hs_trace()
-    L.hs_db_set_trace(D.handle, C.byref(tr))
 
     def step(ev_pair=None):
         if ev_pair is not None:
@@ -428,11 +522,6 @@ def run_ours(args, world, rank, local):
         b.record(stream)
     stream.synchronize()
     t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
     clocks = ClockSampler(uuid) if rank == 0 else None
     if world > 1:
         torch.distributed.barrier()
@@ -485,18 +574,28 @@ def run_ours(args, world, rank, local):
         return
 
     # Roofline of the scan kernel, T_roof = max(B / HBM, Ops / P_int): Ops = one
-    # integer add per cell (the per-shift compare, about 1/ss of that, is left
-    # out, so `achieved` errs low); P_int = SMs x 128 INT32 lanes x max SM
-    # clock; B = the residues, and per pair its schedule entry (4 B) and two
-    # offsets (16 B) read and its score (4 B) written.
+    # integer add per cell plus one compare per shift (both counted by the
+    # kernel); P_int = the measured 32-bit integer add rate of this GPU
+    # (libhspeak.so, above), else SMs x 128 INT32 lanes x max SM clock; B =
+    # the residues, and per pair its schedule entry (4 B) and two offsets
+    # (16 B) read and its score (4 B) written.
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     scan_s = float(np.mean(scan_ms)) / 1000.0
-    achieved = cells_per_search / scan_s / 1e12
-    peak = sms * 128 * 2070e6 / 1e12
+    ops_per_search = cells_per_search + shifts_per_search
+    achieved = ops_per_search / scan_s / 1e12
+    derived = sms * 128 * 2070e6 / 1e12
+    if peaks is not None:
+        peak = peaks["iadd"]["tops"]
+        basis = ("measured: 32-bit integer add issue rate %.2f T/s (libhspeak.so, SM clock %s MHz during it; "
+                 "derived %d SMs x 128 lanes x 2070 MHz = %.2f T/s)" %
+                 (peak, (peaks["clocks"] or {}).get("sm_mhz"), sms, derived))
+    else:
+        peak = derived
+        basis = "%d SMs x 128 INT32 lanes x 2070 MHz (derived)" % sms
     alg_bytes = db.residues + 24 * db.n
     hbm_gbs = measured_hbm_gbs()
-    t_alu_us = cells_per_search / (peak * 1e12) * 1e6
+    t_alu_us = ops_per_search / (peak * 1e12) * 1e6
     t_hbm_us = alg_bytes / (hbm_gbs * 1e9) * 1e6
     traffic = recorded_traffic(cfg["workload"])
 
@@ -504,8 +603,10 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_batched and args.workload == "plain-large":
         batched = batched_section(P, D, db, params, args.seed)
     if world == 1 and not args.no_serving and args.workload == "plain-large":
-        serving = serving_section(P, D, db, params, args.serve_requests)
-    bimodal = bimodal_section(P) if (world == 1 and args.bimodal) else None
+        serving = serving_section(P, D, db, params, args.serve_seconds)
+    bimodal = bimodal_section(P) if (world == 1 and not args.no_bimodal and args.workload == "plain-large") else None
+    small = small_section(P, params, args.seed) if (world == 1 and not args.no_small
+                                                     and args.workload == "plain-large") else None
     cpu_rate, cpu_threads, ns, nres, tcpu = oracle_rate(db, q, args.seed, args.cpu_budget_s) \
         if world == 1 else (None, None, 0, 0, 0.0)
     line = {
@@ -517,20 +618,25 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu" if t_alu_us >= t_hbm_us else "hbm", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic, "kernel": "scan_wide_kernel",
-                     "scan_ms": scan_s * 1000.0, "cells_per_launch": cells_per_search,
+                     "scan_ms": scan_s * 1000.0, "ops_per_launch": ops_per_search,
+                     "cells_per_launch": cells_per_search, "shifts_per_launch": shifts_per_search,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "t_roof_us": max(t_alu_us, t_hbm_us), "t_alu_us": t_alu_us, "t_hbm_us": t_hbm_us,
-                     "peak_basis": "%d SMs x 128 INT32 lanes x 2070 MHz (derived; one add per cell)" % sms,
+                     "peak_basis": basis,
                      "byte_lane_peak": 4 * peak,
-                     "byte_lane_frac": achieved / (4 * peak)},
+                     "byte_lane_frac": cells_per_search / scan_s / 1e12 / (4 * peak)},
         "clocks": clk,
     }
+    if peaks is not None:
+        line["int_peaks"] = peaks
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
         line["serving"] = serving
     if bimodal is not None:
         line["bimodal"] = bimodal
+    if small is not None:
+        line["plain_small"] = small
     if cpu_rate is not None:
         line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                                 "sample": "%d random sequences (%d residues) of the same database, scores only, "

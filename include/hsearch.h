@@ -282,10 +282,15 @@ int hs_search_transfer_bytes(int32_t qlen, int32_t k, int64_t *h2d, int64_t *d2h
  * database, every later search on it records scan_start / scan_stop (two
  * cudaEvent_t created by the caller, or NULL) on its stream around the
  * database scan, and stores in `launches` the number of kernels the search
- * launched.  The struct must stay valid while set; NULL clears the hook. */
+ * launched.  With pack_shifts nonzero, a database-mode hs_search_device that
+ * counts cells (d_cells) stores per pair cells + (shifts << 40) instead,
+ * shifts being the number of shifts whose virtual score was taken
+ * (sum over steps of ls - ss + 1; cells stay below 2^40).  Zero-initialise
+ * the struct.  It must stay valid while set; NULL clears the hook. */
 typedef struct {
     void *scan_start, *scan_stop;
     int32_t launches;
+    int32_t pack_shifts;
 } hs_trace;
 int hs_db_set_trace(hs_db *db, hs_trace *trace);
 

@@ -27,7 +27,8 @@ class hs_params(C.Structure):
 
 
 class hs_trace(C.Structure):
-    _fields_ = [("scan_start", C.c_void_p), ("scan_stop", C.c_void_p), ("launches", C.c_int32)]
+    _fields_ = [("scan_start", C.c_void_p), ("scan_stop", C.c_void_p), ("launches", C.c_int32),
+                ("pack_shifts", C.c_int32)]
 
 
 class hs_batch_tuning(C.Structure):

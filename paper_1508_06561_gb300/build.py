@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhsearch.so")
 SOURCES = ["hs_api.cu", "hs_scan.cu", "hs_topk.cu", "hs_noalloc.cu"]
+# the integer issue-rate microbenchmark behind the scan's roofline (its own library)
+PEAK_LIB = os.path.join(PKG, "libhspeak.so")
+PEAK_SOURCES = ["hs_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,9 +38,9 @@ def _deps():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAK_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAK_LIB))
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
@@ -58,19 +61,22 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(len(SOURCES) + len(PEAK_SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES + PEAK_SOURCES))
     if verbose:
         for _, err in results:
             if err:
                 print(err)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-Xlinker",
-                             "--version-script=" + os.path.join(CSRC, "exports.map"), "-o", tmp] + [o for o, _ in results]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
+    objs = [o for o, _ in results]
+    for lib, srcs, script in ((LIB, SOURCES, "exports.map"), (PEAK_LIB, PEAK_SOURCES, "peak_exports.map")):
+        tmp = lib + ".tmp%d" % os.getpid()
+        mine = [o for o in objs if os.path.basename(o)[:-2] + ".cu" in srcs]
+        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-Xlinker",
+                                 "--version-script=" + os.path.join(CSRC, script), "-o", tmp] + mine
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
+        os.replace(tmp, lib)
     return LIB
 
 

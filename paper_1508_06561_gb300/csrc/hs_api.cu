@@ -147,6 +147,7 @@ static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams
     sp.min_score = INT_MIN;
     sp.mode = p->mode;
     sp.pair16 = (int64_t)range * (qlen + 3) <= 65535;
+    sp.pack_shifts = 0;
     return HS_OK;
 }
 
@@ -381,6 +382,7 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
     if (rc != HS_OK) return rc;
     kp.s.index_base = db->index_base;
     kp.s.min_score = min_score;
+    kp.s.pack_shifts = db->trace && db->trace->pack_shifts && d_cells && kp.s.mode == HS_MODE_DB;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Workspace ws = carve_workspace(d_workspace, db->n, qlen, k);

@@ -273,7 +273,9 @@ __device__ __forceinline__ void fwd_chunk(const uint32_t *prof, int R, const uin
 __device__ __forceinline__ void lane_best1(uint32_t acc, int k, int nshift, int32_t off, int32_t &bv, int32_t &bk)
 {
     const int32_t v = (int32_t)acc - off;
-    if (k < nshift && v > bv) { bv = v; bk = k; }
+    bool keep;
+    const int32_t m = __vibmax_s32(bv, v, &keep);      // keep: bv >= v (the earlier shift stays)
+    if (k < nshift) { bk = keep ? bk : k; bv = m; }
 }
 
 // shifts ascend within a chunk, so a strict '>' keeps the lowest k
@@ -405,11 +407,11 @@ __device__ __forceinline__ uint32_t unit_key_at(const uint32_t *prof, int R, con
     else fwd_chunk<true>(prof, R, tb, col + k0, 0, ss, flush, A);
     const uint32_t c = 0xFFFFu - (uint32_t)k0;
     const int nv = nshift - k0;                     // shifts of this chunk inside the step, >= 1
-    uint32_t key = __byte_perm(A.p01, c, 0x1054);   // sum of shift k0 above 0xFFFF - k0
-    if (nv > 1) key = max(key, __byte_perm(A.p01, c - 1u, 0x3254));
-    if (nv > 2) key = max(key, __byte_perm(A.p23, c - 2u, 0x1054));
-    if (nv > 3) key = max(key, __byte_perm(A.p23, c - 3u, 0x3254));
-    return key;
+    const uint32_t y0 = __byte_perm(A.p01, c, 0x1054);   // sum of shift k0 above 0xFFFF - k0
+    const uint32_t y1 = nv > 1 ? __byte_perm(A.p01, c - 1u, 0x3254) : 0u;
+    const uint32_t y2 = nv > 2 ? __byte_perm(A.p23, c - 2u, 0x1054) : 0u;
+    const uint32_t y3 = nv > 3 ? __byte_perm(A.p23, c - 3u, 0x3254) : 0u;
+    return max(__vimax3_u32(y0, y1, y2), y3);
 }
 
 __device__ __forceinline__ uint32_t unit_key(const uint32_t *prof, int R, int qlen, const Plan &g, int k0,

@@ -36,6 +36,7 @@ struct SParams {
     int32_t min_score;                  // replay only hits scoring >= this (threshold search)
     int32_t mode;                       // HS_MODE_DB or HS_MODE_FULL
     int32_t pair16;                     // 16-bit chunk sums suffice: (max-min) * (qlen+3) <= 65535
+    int32_t pack_shifts;                // cell counts also carry the shifts scanned, << 40 (profiling)
 };
 
 // The matrix (for building profiles) plus the scoring parameters.

@@ -315,7 +315,8 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         }
         // consume (Fig. 1: drop what the step took from both) and score incrementally (A17)
         if (busy) {
-            L.cells += (int64_t)(g.ls - g.ss + 1) * g.ss;
+            const int64_t nshift = g.ls - g.ss + 1;
+            L.cells += nshift * g.ss + (sp.pack_shifts ? nshift << 40 : 0);
             int32_t gap = 0;
             if (kstar > 0) gap = (L.step == 0) ? sp.pgp * kstar : sp.gop + (kstar - 1) * sp.gep;
             L.score += vmax - gap;

@@ -45,6 +45,11 @@ inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
     for (int n = 0; n < 4; n++) r |= (uint32_t)((v >> (8 * ((s >> (4 * n)) & 7))) & 0xFF) << (8 * n);
     return r;
 }
+// DPX maxima, as documented: the three-way unsigned maximum, and the
+// maximum of two signed values with a flag telling whether the first won
+// (a >= b).
+inline unsigned __vimax3_u32(unsigned a, unsigned b, unsigned c) { return std::max(a, std::max(b, c)); }
+inline int __vibmax_s32(int a, int b, bool *pred) { *pred = a >= b; return a >= b ? a : b; }
 inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
 
 // ---- lockstep warp (and CTA barrier) ----------------------------------------

@@ -107,3 +107,19 @@ def test_ops_to_rows_roundtrip():
     assert rq.tolist() == [1, 2, 3, 255] and rt.tolist() == [4, 255, 255, 5]
     with pytest.raises(ValueError):
         P.ops_to_rows(ops[:2], q, t)
+
+
+def test_peak_library_exports_exactly_its_header():
+    """The integer issue-rate microbenchmark (the scan roofline's peak) is
+    its own library; it exports include/hspeak.h's functions and nothing else."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if not nm:
+        pytest.skip("nm not available")
+    build.build()
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(os.path.dirname(HEADER), "hspeak.h")).read(), flags=re.S)
+    declared = sorted(set(re.findall(r"\b(hsp_[a-z_0-9]+)\s*\(", text)))
+    out = subprocess.run([nm, "-D", "--defined-only", build.PEAK_LIB], capture_output=True, text=True, check=True).stdout
+    exported = sorted({line.split()[-1] for line in out.splitlines() if line.split()[1:2] and line.split()[1] in "TW"})
+    assert exported == declared == ["hsp_measure", "hsp_ops_per_thread_trip"]

@@ -219,3 +219,40 @@ def test_batched_rejects_full_mode():
     with pytest.raises(P.HsError):
         P.search_batch(D, [synth.residues(rng, 10)], 2, p_full(P.Params()))
     D.close()
+
+
+def test_trace_hook_packs_shift_counts():
+    """With the trace hook's pack_shifts set, a database-mode search that
+    counts cells stores per pair cells + (shifts << 40), shifts being the
+    shifts whose virtual score was taken (sum of ls - ss + 1 over the steps
+    of every round).  Both parts equal the independent step trace's
+    (tests/test_oracle_steps.py, Fig. 1); without the flag the plain cell
+    counts come back."""
+    import ctypes as C
+
+    from paper_1508_06561_gb300 import _lib
+    from test_oracle_steps import trace_round
+    rng = np.random.default_rng(77)
+    db = synth.db_from_lengths(rng, np.concatenate([[0, 1, 3], synth.lognormal_lengths(rng, 300, 200, 0.7, 1, 3000)]))
+    q = synth.residues(rng, 90)
+    M = O.blosum62()
+    for params, op in ((P.Params(), O.paper_params()),
+                       (P.Params(rounds=2, lfactor_q16=50000), O.paper_params(rounds=2, lfactor_q16=50000))):
+        D = P.Database(db.codes, db.offsets)
+        tr = _lib.hs_trace()
+        tr.pack_shifts = 1
+        _lib.lib().hs_db_set_trace(D.handle, C.byref(tr))
+        out = P.search_device(D, torch.from_numpy(q).cuda(), 5, params, seed=21, want_cells=True)
+        torch.cuda.synchronize()
+        packed = out["cells"].cpu().numpy()[: D.n]
+        _lib.lib().hs_db_set_trace(D.handle, None)
+        _, _, _, plain = run_device(D, q, 5, params, 21)
+        for d in range(db.n):
+            cells = shifts = 0
+            for r in range(op.rounds):
+                _, _, steps, c, _ = trace_round(q, db.seq(d), M, op, 21, d, r)
+                cells += c
+                shifts += sum(ls - ss + 1 for ls, ss, _ in steps)
+            assert int(packed[d]) & ((1 << 40) - 1) == cells == int(plain[d])
+            assert int(packed[d]) >> 40 == shifts
+        D.close()
