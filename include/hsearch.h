@@ -123,13 +123,23 @@ int hs_db_load(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs,
 int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seqs, int64_t index_base,
                      void *stream, hs_db **out);
 
-/* Work schedule of the scan (results never depend on it).
+/* Work schedule of the scan (results never depend on it; no counterpart in
+ * the paper, whose program visits the database in file order).
  * HS_SCHEDULE_LENGTH (the default after loading): longest targets first,
- * targets of >= 2048 letters one per warp -- the length-binned layout.
- * HS_SCHEDULE_INPUT: database order, for comparing load balance. */
+ * equal lengths in database order, targets of >= 2048 letters one per warp
+ * -- the length-binned layout.  The order is built on the device by a
+ * stable radix sort of the lengths, with the residues before each schedule
+ * position.  HS_SCHEDULE_INPUT: database order, for comparing load balance.
+ * Enqueued on `stream` and waited for; allocates scratch for the sort and
+ * frees it.  HS_EINVAL, HS_ENOMEM, HS_ECUDA. */
 #define HS_SCHEDULE_LENGTH 0
 #define HS_SCHEDULE_INPUT  1
 int hs_db_set_schedule(hs_db *db, int32_t schedule, void *stream);
+
+/* The current schedule, copied to host buffers (either may be NULL):
+ * order_out[n_seqs] = database index at each scan position (shard-local),
+ * cumres_out[n_seqs + 1] = residues before each position.  Synchronous. */
+int hs_db_get_schedule(const hs_db *db, int32_t *order_out, int64_t *cumres_out);
 
 /* The global index of a database's first sequence (0 unless a shard). */
 int hs_db_index_base(const hs_db *db, int64_t *index_base);

@@ -109,6 +109,14 @@ class Database:
         SCHEDULE_INPUT (database order).  Results do not depend on it."""
         check(lib().hs_db_set_schedule(self.handle, schedule, _stream_ptr(stream)), "hs_db_set_schedule")
 
+    def schedule(self):
+        """(order, cumres): database index at each scan position and the
+        residues before each position (hs_db_get_schedule)."""
+        order = np.zeros(max(self.n, 1), np.int32)
+        cumres = np.zeros(self.n + 1, np.int64)
+        check(lib().hs_db_get_schedule(self.handle, order.ctypes.data, cumres.ctypes.data), "hs_db_get_schedule")
+        return order[: self.n], cumres
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().hs_db_free(self._h)

@@ -66,6 +66,7 @@ def lib():
     L.hs_db_load_shard.argtypes = [vp, vp, i64, i64, vp, P(vp)]
     L.hs_db_index_base.argtypes = [vp, P(i64)]
     L.hs_db_set_schedule.argtypes = [vp, i32, vp]
+    L.hs_db_get_schedule.argtypes = [vp, vp, vp]
     L.hs_search_threshold.argtypes = [vp, vp, i32, P(hs_params), i32, i32, u64, vp, vp, P(i32), P(i64), vp, i64, P(i64)]
     L.hs_db_free.argtypes = [vp]
     L.hs_db_free.restype = None
@@ -92,7 +93,7 @@ def lib():
                  "hs_search_transfer_bytes", "hs_db_set_trace", "hs_search_device_noalloc",
                  "hs_db_load_shard", "hs_db_index_base", "hs_search_threshold",
                  "hs_search_batch_workspace_size", "hs_search_batch_device", "hs_search_batch",
-                 "hs_db_set_schedule"):
+                 "hs_db_set_schedule", "hs_db_get_schedule"):
         getattr(L, name).restype = C.c_int
     _L = L
     return L

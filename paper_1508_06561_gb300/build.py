@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhsearch.so")
-SOURCES = ["hs_api.cu", "hs_scan.cu", "hs_topk.cu", "hs_noalloc.cu"]
+SOURCES = ["hs_api.cu", "hs_scan.cu", "hs_topk.cu", "hs_noalloc.cu", "hs_sort.cu"]
 # the integer issue-rate microbenchmark behind the scan's roofline (its own library)
 PEAK_LIB = os.path.join(PKG, "libhspeak.so")
 PEAK_SOURCES = ["hs_peak.cu"]

@@ -164,7 +164,6 @@ struct hs_db {
     int64_t *d_offsets = nullptr;
     int32_t *d_order = nullptr;
     int64_t *d_cumres = nullptr;            // residues before each position of the schedule
-    std::vector<int32_t> lens;              // lengths in database order
     std::vector<int32_t> sorted_len;        // lengths in schedule order (non-increasing unless input order)
     int32_t schedule = HS_SCHEDULE_LENGTH;
     // host-API state (grown on demand)
@@ -288,9 +287,6 @@ int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seq
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->device);
     if (e != cudaSuccess) { hs_db_free(db); return from_cuda(e); }
 
-    db->lens.resize((size_t)n_seqs);
-    for (int64_t i = 0; i < n_seqs; i++) db->lens[i] = (int32_t)(offsets[i + 1] - offsets[i]);
-
     e = dev_malloc(&db->d_codes, (size_t)nres + kCodesPad);
     if (e == cudaSuccess) e = dev_malloc(&db->d_offsets, sizeof(int64_t) * (size_t)(n_seqs + 1));
     if (e == cudaSuccess) e = dev_malloc(&db->d_order, sizeof(int32_t) * (size_t)std::max<int64_t>(n_seqs, 1));
@@ -308,27 +304,39 @@ int hs_db_load_shard(const uint8_t *codes, const int64_t *offsets, int64_t n_seq
 
 int hs_db_set_schedule(hs_db *db, int32_t schedule, void *stream)
 {
+    NvtxRange r("hs_db_set_schedule");
     if (!db || (schedule != HS_SCHEDULE_LENGTH && schedule != HS_SCHEDULE_INPUT)) return HS_EINVAL;
     const int64_t n = db->n;
-    // the schedule: longest first (ties by index), or database order
-    std::vector<int32_t> order((size_t)n);
-    std::iota(order.begin(), order.end(), 0);
-    if (schedule == HS_SCHEDULE_LENGTH)
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return db->lens[a] > db->lens[b]; });
-    db->sorted_len.resize((size_t)n);
-    std::vector<int64_t> cumres((size_t)n + 1, 0);
-    for (int64_t i = 0; i < n; i++) {
-        db->sorted_len[i] = db->lens[order[i]];
-        cumres[i + 1] = cumres[i] + db->sorted_len[i];
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaSuccess;
-    if (n > 0) e = cudaMemcpyAsync(db->d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_cumres, cumres.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
+    // the order is built on the device (hs_sort.cu); the host keeps the
+    // lengths in schedule order for the role split and the long prefix
+    void *scratch = nullptr;
+    int32_t *d_len = nullptr;
+    std::vector<int32_t> len((size_t)n);
+    cudaError_t e = dev_malloc(&scratch, schedule_scratch_bytes(n));
+    if (e == cudaSuccess) e = dev_malloc(&d_len, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1));
+    if (e == cudaSuccess)
+        e = build_schedule(db->d_offsets, n, db->maxlen, schedule == HS_SCHEDULE_LENGTH, db->d_order, db->d_cumres,
+                           d_len, scratch, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(len.data(), d_len, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    cudaFree(d_len);
     if (e != cudaSuccess) return from_cuda(e);
+    db->sorted_len.swap(len);
     db->schedule = schedule;
     return HS_OK;
+}
+
+int hs_db_get_schedule(const hs_db *db, int32_t *order_out, int64_t *cumres_out)
+{
+    if (!db) return HS_EINVAL;
+    cudaError_t e = cudaSuccess;
+    if (order_out && db->n > 0)
+        e = cudaMemcpy(order_out, db->d_order, sizeof(int32_t) * (size_t)db->n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && cumres_out)
+        e = cudaMemcpy(cumres_out, db->d_cumres, sizeof(int64_t) * (size_t)(db->n + 1), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? HS_OK : from_cuda(e);
 }
 
 int hs_db_index_base(const hs_db *db, int64_t *index_base)

@@ -98,6 +98,13 @@ constexpr int kMaxChunks = 8192;
 constexpr int kBatchShortLen = 512;     // batched scan: queries up to this long form the short class
 constexpr int kDefaultChunks = 1024;
 
+// The scan schedule (hs_sort.cu): d_order = database indices longest first
+// (ties in database order) or in database order; d_sorted_len = their
+// lengths; d_cumres[i] = residues before schedule position i (n + 1).
+size_t schedule_scratch_bytes(int64_t n);
+cudaError_t build_schedule(const int64_t *d_offsets, int64_t n, int32_t maxlen, bool by_length, int32_t *d_order,
+                           int64_t *d_cumres, int32_t *d_sorted_len, void *d_scratch, cudaStream_t st);
+
 size_t workspace_bytes(int64_t n, int32_t qlen, int32_t k);
 Workspace carve_workspace(void *base, int64_t n, int32_t qlen, int32_t k);
 int64_t slot_stride_for(int32_t qlen);

@@ -1,0 +1,218 @@
+// hs_sort.cu -- the database's scan schedule, built on the device.
+//
+// The scan visits the database longest first (ties in database order), so
+// that the long targets start early and the short ones fill the end of the
+// scan.  The order is a stable least-significant-digit radix sort of the
+// key (maxlen - length) with 8-bit digits: per pass, every block counts the
+// digits of its tile, one scan turns the counts (digit-major, block-minor)
+// into each block's first output position per digit, and every block
+// scatters its tile in index order -- equal digits keep their relative
+// order (ranks within a warp by __match_any_sync, across the block's warps
+// by per-warp counts) -- so after the last pass equal lengths stay in
+// database order.  Then the lengths in schedule order and their prefix sums
+// (the residues before each schedule position, which the batched scan cuts
+// into equal chunks).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+namespace {
+
+constexpr int kSortThreads = 256;       // one thread per digit value
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortTile = 4096;         // elements per block and pass
+constexpr int kScanThreads = 1024;
+
+__global__ void order_keys_kernel(const int64_t *offsets, int64_t n, int32_t maxlen, bool by_length,
+                                  uint32_t *keys, int32_t *idx)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t len = (int32_t)(offsets[i + 1] - offsets[i]);
+        keys[i] = by_length ? (uint32_t)(maxlen - len) : 0u;    // ascending key = longest first
+        idx[i] = (int32_t)i;
+    }
+}
+
+// Digit counts of one tile: hist[digit * nblocks + block].
+__global__ void __launch_bounds__(kSortThreads) radix_count_kernel(const uint32_t *keys, int64_t n, int shift,
+                                                                   uint32_t *hist)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * kSortTile, t1 = min(n, t0 + kSortTile);
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += kSortThreads) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// In-place exclusive prefix sum of m counts by one block, 1024 at a time.
+__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(uint32_t *a, int64_t m)
+{
+    __shared__ uint32_t warp_sum[kScanThreads / 32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < m; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < m ? a[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;                     // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t before = carry + (warp ? warp_sum[warp - 1] : 0u);
+        if (i < m) a[i] = before + x - v;
+        __syncthreads();                            // every thread has read carry
+        if (threadIdx.x == kScanThreads - 1) carry = before + x;
+        __syncthreads();
+    }
+}
+
+// Scatter one tile in index order to its digits' positions (stable).
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint32_t *kin, const int32_t *iin,
+                                                                     uint32_t *kout, int32_t *iout, int64_t n,
+                                                                     int shift, const uint32_t *first)
+{
+    __shared__ uint32_t next[256];                  // the next output position of each digit
+    __shared__ uint32_t cnt[kSortWarps][256];       // this round's digits per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    next[threadIdx.x] = first[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+    const int64_t t0 = (int64_t)blockIdx.x * kSortTile, t1 = min(n, t0 + kSortTile);
+    for (int64_t r = t0; r < t1; r += kSortThreads) {
+        for (int j = threadIdx.x; j < kSortWarps * 256; j += kSortThreads) (&cnt[0][0])[j] = 0u;
+        __syncthreads();
+        const int64_t i = r + threadIdx.x;
+        const bool valid = i < t1;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t d = valid ? (key >> shift) & 255u : 256u;       // 256: no digit of a real key
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));          // earlier lanes with this digit
+        if (valid && rank == 0) cnt[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = next[d] + (uint32_t)rank;
+            for (int w = 0; w < warp; w++) pos += cnt[w][d];            // earlier warps with this digit
+            kout[pos] = key;
+            iout[pos] = iin[i];
+        }
+        __syncthreads();                            // every thread has read next[] and cnt[]
+        uint32_t tot = 0;
+        for (int w = 0; w < kSortWarps; w++) tot += cnt[w][threadIdx.x];
+        next[threadIdx.x] += tot;
+        __syncthreads();
+    }
+}
+
+// Lengths in schedule order.
+__global__ void sorted_lengths_kernel(const int64_t *offsets, const int32_t *order, int64_t n, int32_t *len)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = order[i];
+        len[i] = (int32_t)(offsets[d + 1] - offsets[d]);
+    }
+}
+
+// cumres[0] = 0, cumres[i + 1] = cumres[i] + len[i], by one block.
+__global__ void __launch_bounds__(kScanThreads) residue_prefix_kernel(const int32_t *len, int64_t n, int64_t *cumres)
+{
+    __shared__ int64_t warp_sum[kScanThreads / 32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { carry = 0; cumres[0] = 0; }
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        int64_t x = i < n ? len[i] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        const int64_t incl = carry + (warp ? warp_sum[warp - 1] : 0) + x;
+        if (i < n) cumres[i + 1] = incl;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry = incl;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// Scratch carve-up: two key buffers, two index buffers and the digit
+// counts, each 256-byte aligned.
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t schedule_scratch_bytes(int64_t n)
+{
+    const int64_t nb = std::max<int64_t>(1, (n + kSortTile - 1) / kSortTile);
+    const size_t a = (size_t)std::max<int64_t>(n, 1) * 4;
+    return 4 * round256(a) + round256((size_t)nb * 256 * 4);
+}
+
+cudaError_t build_schedule(const int64_t *d_offsets, int64_t n, int32_t maxlen, bool by_length, int32_t *d_order,
+                           int64_t *d_cumres, int32_t *d_sorted_len, void *d_scratch, cudaStream_t st)
+{
+    const int64_t nb = std::max<int64_t>(1, (n + kSortTile - 1) / kSortTile);
+    const size_t a = (size_t)std::max<int64_t>(n, 1);
+    char *p = static_cast<char *>(d_scratch);
+    auto take = [&](size_t bytes) { char *q = p; p += round256(bytes); return q; };
+    uint32_t *k0 = reinterpret_cast<uint32_t *>(take(a * 4)), *k1 = reinterpret_cast<uint32_t *>(take(a * 4));
+    int32_t *i0 = reinterpret_cast<int32_t *>(take(a * 4)), *i1 = reinterpret_cast<int32_t *>(take(a * 4));
+    uint32_t *hist = reinterpret_cast<uint32_t *>(take((size_t)nb * 256 * 4));
+    if (n == 0) {
+        residue_prefix_kernel<<<1, kScanThreads, 0, st>>>(d_sorted_len, 0, d_cumres);
+        return cudaGetLastError();
+    }
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    order_keys_kernel<<<grid, 256, 0, st>>>(d_offsets, n, maxlen, by_length, k0, i0);
+    cudaError_t e = cudaGetLastError();
+    // passes over the key's significant bits, ping-ponging between the
+    // scratch buffers; d_order is written only once the order is complete
+    int bits = 0;
+    if (by_length)
+        while (bits < 32 && (maxlen >> bits) != 0) bits++;
+    uint32_t *kin = k0, *kout = k1;
+    int32_t *iin = i0, *iout = i1;
+    for (int shift = 0; shift < bits && e == cudaSuccess; shift += 8) {
+        radix_count_kernel<<<(int)nb, kSortThreads, 0, st>>>(kin, n, shift, hist);
+        exclusive_scan_kernel<<<1, kScanThreads, 0, st>>>(hist, nb * 256);
+        radix_scatter_kernel<<<(int)nb, kSortThreads, 0, st>>>(kin, iin, kout, iout, n, shift, hist);
+        e = cudaGetLastError();
+        std::swap(kin, kout);
+        std::swap(iin, iout);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, iin, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    sorted_lengths_kernel<<<grid, 256, 0, st>>>(d_offsets, d_order, n, d_sorted_len);
+    residue_prefix_kernel<<<1, kScanThreads, 0, st>>>(d_sorted_len, n, d_cumres);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import HIT_DTYPE, Database, Params, search, search_threshold
+from . import HIT_DTYPE, Database, Params, device_result_to_host, search, search_device, search_threshold
 
 
 def split_offsets(offsets, nshards: int):
@@ -74,35 +74,62 @@ class ShardedDatabase:
         import torch
         self.devices = list(devices)
         self.ranges = split_offsets(offsets, len(self.devices))
-        self.shards = []
+        self.shards, self.streams = [], []
+        self._bufs = [None] * len(self.devices)      # per shard: device buffers of the last search
         prev = torch.cuda.current_device()
         try:
             for dev, (lo, hi) in zip(self.devices, self.ranges):
                 torch.cuda.set_device(dev)
                 c, o, base = shard_arrays(codes, offsets, lo, hi)
                 self.shards.append(Database(c, o, index_base=base))
+                self.streams.append(torch.cuda.Stream(dev))
         finally:
             torch.cuda.set_device(prev)
         self.n = sum(s.n for s in self.shards)
 
-    def _each(self, fn):
+    def search(self, query, k: int, params: Params | None = None, seed: int = 0):
+        """Every shard's search is enqueued on its own stream (and device)
+        before any is waited for, so the shards run at the same time; then
+        the k best records are merged on the host."""
         import torch
+        q = np.ascontiguousarray(query, dtype=np.uint8)
+        qh = torch.from_numpy(q).pin_memory()
         prev = torch.cuda.current_device()
+        outs = []
         try:
-            out = []
-            for dev, db in zip(self.devices, self.shards):
+            for i, (dev, db, st) in enumerate(zip(self.devices, self.shards, self.streams)):
                 torch.cuda.set_device(dev)
-                out.append(fn(db))
-            return out
+                with torch.cuda.stream(st):
+                    qd = qh.to(torch.device("cuda", dev), non_blocking=True)
+                    b = self._bufs[i]
+                    fits = b is not None and b["k"] == k and b["qlen"] == len(q)
+                    out = search_device(db, qd, k, params, seed, stream=st,
+                                        workspace=b["out"]["workspace"] if fits else None,
+                                        out=b["out"] if fits else None)
+                    self._bufs[i] = {"k": k, "qlen": len(q), "out": out, "q": qd}
+                outs.append(out)
+            parts = []
+            for dev, st, out in zip(self.devices, self.streams, outs):
+                torch.cuda.set_device(dev)
+                st.synchronize()
+                parts.append(device_result_to_host(out))
         finally:
             torch.cuda.set_device(prev)
-
-    def search(self, query, k: int, params: Params | None = None, seed: int = 0):
-        parts = self._each(lambda db: search(db, query, k, params, seed))
         return merge_hits(parts, k)
 
     def search_threshold(self, query, threshold: int, max_hits: int, params: Params | None = None, seed: int = 0):
-        res = self._each(lambda db: search_threshold(db, query, threshold, max_hits, params, seed))
+        """One host thread per shard (the library call releases the GIL), so
+        the shards' searches run at the same time; then the merge."""
+        import concurrent.futures as cf
+
+        import torch
+
+        def one(i):
+            torch.cuda.set_device(self.devices[i])
+            return search_threshold(self.shards[i], query, threshold, max_hits, params, seed, stream=self.streams[i])
+
+        with cf.ThreadPoolExecutor(len(self.shards)) as ex:
+            res = list(ex.map(one, range(len(self.shards))))
         hits, ops = merge_hits([(h, o) for h, o, _ in res], max_hits)
         return hits, ops, sum(a for _, _, a in res)
 

@@ -73,3 +73,53 @@ def test_load_balance_workload_matches_oracle_under_both_schedules():
             check_hits(db, q, M, op, s, hits, ops, ref, k)
             check_hits(db, q, M, op, s, batch[i][0], batch[i][1], ref, k)
     D.close()
+
+
+def host_order(lengths):
+    """The schedule the scan needs: longest first, equal lengths in database
+    order (a stable sort of -length)."""
+    return np.argsort(-np.asarray(lengths, np.int64), kind="stable")
+
+
+def check_schedule(D, lengths):
+    L = np.asarray(lengths, np.int64)
+    order, cumres = D.schedule()
+    want = host_order(L)
+    assert np.array_equal(order, want)
+    assert np.array_equal(cumres, np.concatenate([[0], np.cumsum(L[want])]))
+    D.set_schedule(P.Database.SCHEDULE_INPUT)
+    order, cumres = D.schedule()
+    assert np.array_equal(order, np.arange(len(L))) and np.array_equal(cumres, np.concatenate([[0], np.cumsum(L)]))
+    D.set_schedule(P.Database.SCHEDULE_LENGTH)
+    order, _ = D.schedule()
+    assert np.array_equal(order, want)
+
+
+def test_length_order_is_built_on_the_device_and_stable():
+    """The length-binned schedule comes from the device radix sort: it equals
+    a stable host sort on the database-scale workload (570k sequences), on a
+    database made almost only of ties, on lengths that need all three 8-bit
+    digit passes (up to 300,000 letters), and on the degenerate cases."""
+    db, _, _ = synth.plain_large()
+    D = P.Database(db.codes, db.offsets)
+    check_schedule(D, db.lengths())
+    D.close()
+    rng = np.random.default_rng(9)
+    cases = [
+        rng.choice([0, 1, 7, 300, 301, 2048], 50_000),                          # ties everywhere
+        np.concatenate([rng.integers(0, 400, 20_000), [300_000, 65_536, 65_535, 256, 255, 300_000]]),
+        np.zeros(10, np.int64),                                                  # all empty
+        np.array([5]),
+        np.array([], np.int64),
+    ]
+    for lengths in cases:
+        d = synth.db_from_lengths(rng, lengths)
+        D = P.Database(d.codes, d.offsets)
+        check_schedule(D, d.lengths())
+        if d.n:
+            q = synth.residues(rng, 40)
+            h0, o0 = P.search(D, q, 5, seed=2)
+            D.set_schedule(P.Database.SCHEDULE_INPUT)
+            h1, o1 = P.search(D, q, 5, seed=2)
+            assert np.array_equal(h0, h1) and np.array_equal(o0, o1)
+        D.close()
