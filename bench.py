@@ -255,16 +255,23 @@ def batched_section(P, D, db, params, seed, reps=3):
     seeds = torch.full((len(qs),), seed, dtype=torch.int64, device="cuda")
     mq = int(max(len(q) for q in qs))
     st = torch.cuda.Stream()
-    with torch.cuda.stream(st):
-        out = P.search_batch_device(D, cat, offd, seeds, mq, k, params, best, st)     # warm-up
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        for _ in range(reps):
-            P.search_batch_device(D, cat, offd, seeds, mq, k, params, best, st, out["workspace"], out)
-        b.record(st)
-    st.synchronize()
-    assert int(out["status"].item()) == 0
-    t_batch = a.elapsed_time(b) / 1000.0 / reps
+
+    def timed_batch(tuning):
+        with torch.cuda.stream(st):
+            out = P.search_batch_device(D, cat, offd, seeds, mq, k, params, tuning, st)     # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                P.search_batch_device(D, cat, offd, seeds, mq, k, params, tuning, st, out["workspace"], out)
+            b.record(st)
+        st.synchronize()
+        assert int(out["status"].item()) == 0
+        used = int(out["ops_used"].item())
+        return a.elapsed_time(b) / 1000.0 / reps, out["hits"].cpu().numpy().copy(), out["ops"][:used].cpu().numpy().copy()
+
+    t_default, h_def, o_def = timed_batch(autotune.DEFAULT)
+    t_batch, h_tuned, o_tuned = timed_batch(best)
+    same = bool(np.array_equal(h_def, h_tuned) and np.array_equal(o_def, o_tuned))
     # the same queries, one plain device search each
     qd = [torch.from_numpy(q).cuda() for q in qs]
     longest = int(np.argmax([len(q) for q in qs]))
@@ -286,6 +293,9 @@ def batched_section(P, D, db, params, seed, reps=3):
             "value": res / t_batch, "unit": UNIT, "ms_per_batch": t_batch * 1000.0,
             "plain_same_queries": res / t_plain, "plain_ms": t_plain * 1000.0,
             "speedup_vs_plain": t_plain / t_batch, "tuning": best,
+            "default_tuning": autotune.DEFAULT, "default_ms_per_batch": t_default * 1000.0,
+            "tuned_speedup_vs_default": t_default / t_batch, "tuned_output_identical": same,
+            "tuning_evaluated": len(tune_s),
             "tuning_candidates_ms": {kk: v * 1000.0 for kk, v in tune_s.items()}}
 
 

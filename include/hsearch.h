@@ -228,12 +228,24 @@ int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
  * Queries are concatenated: query i is queries[qoffsets[i] .. qoffsets[i+1]).
  * Hits of query i occupy hits[i*k .. i*k + min(k, n_seqs)); their ops
  * offsets index one ops buffer shared by all queries.
- * tuning (optional, NULL = defaults): chunks = work items per query over the
- * database (<= 8192; default 1024), ctas_per_sm = resident CTAs per SM
- * (0 = as many as fit).  Results never depend on the tuning. */
+ * tuning (optional, NULL = defaults; no counterpart in the paper; every
+ * field 0 = its default, results never depend on the tuning):
+ *   chunks          work items per query over the database (<= 8192; 1024);
+ *   warps           warps per scan CTA, 24 or 12 (default: the widest that
+ *                   fits the class's profile; a value that does not fit is
+ *                   ignored);
+ *   flat_min_chunks a step is scored as units of the flat list when it has
+ *                   at least this many 4-shift chunks (16) ...
+ *   flat_max_iters  ... or at most this many iterations per chunk (128);
+ *                   the others get a warp's lane grid;
+ *   long_len        targets at least this long are taken one per warp (2048).
+ * Negative values: HS_EINVAL. */
 typedef struct {
     int32_t chunks;
-    int32_t ctas_per_sm;
+    int32_t warps;
+    int32_t flat_min_chunks;
+    int32_t flat_max_iters;
+    int32_t long_len;
 } hs_batch_tuning;
 
 /* Workspace for hs_search_batch_device (total_qlen = sum of query lengths,

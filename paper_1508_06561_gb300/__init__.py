@@ -172,7 +172,13 @@ def _tuning(tuning):
         return None
     if isinstance(tuning, _lib.hs_batch_tuning):
         return tuning
-    return _lib.hs_batch_tuning(int(tuning.get("chunks", 0)), int(tuning.get("ctas_per_sm", 0)))
+    unknown = set(tuning) - set(TUNING_KEYS)
+    if unknown:
+        raise ValueError("unknown tuning keys: %s" % sorted(unknown))
+    return _lib.hs_batch_tuning(*[int(tuning.get(key, 0)) for key in TUNING_KEYS])
+
+
+TUNING_KEYS = ("chunks", "warps", "flat_min_chunks", "flat_max_iters", "long_len")
 
 
 def _pack_queries(queries):
@@ -187,7 +193,8 @@ def search_batch(db: Database, queries, k: int, params: Params | None = None, se
                  stream=None):
     """hs_search_batch: many queries in one scan launch.  Returns a list of
     (hits, ops) per query, each exactly what search() gives for that query
-    and its seed (seeds default to 0).  tuning: {"chunks", "ctas_per_sm"}."""
+    and its seed (seeds default to 0).  tuning: a dict with any of
+    TUNING_KEYS (hs_batch_tuning; absent or 0 = the default)."""
     cat, off = _pack_queries(queries)
     nq = len(off) - 1
     sd = np.zeros(nq, np.uint64) if seeds is None else np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))

@@ -32,7 +32,8 @@ class hs_trace(C.Structure):
 
 
 class hs_batch_tuning(C.Structure):
-    _fields_ = [("chunks", C.c_int32), ("ctas_per_sm", C.c_int32)]
+    _fields_ = [("chunks", C.c_int32), ("warps", C.c_int32), ("flat_min_chunks", C.c_int32),
+                ("flat_max_iters", C.c_int32), ("long_len", C.c_int32)]
 
 
 class HsError(RuntimeError):

@@ -148,6 +148,8 @@ static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams
     sp.mode = p->mode;
     sp.pair16 = (int64_t)range * (qlen + 3) <= 65535;
     sp.pack_shifts = 0;
+    sp.flat_min_chunks = kFlatMinChunks;
+    sp.flat_max_iters = kFlatMaxIters;
     return HS_OK;
 }
 
@@ -660,7 +662,11 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     if (k < 0 || k > HS_MAX_K || ops_cap < 0) return HS_EINVAL;
     const int32_t nchunk = tuning && tuning->chunks > 0 ? tuning->chunks : kDefaultChunks;
     if (nchunk > kMaxChunks) return HS_EINVAL;
-    const int ctas_per_sm = tuning ? tuning->ctas_per_sm : 0;
+    if (tuning && (tuning->warps < 0 || tuning->flat_min_chunks < 0 || tuning->flat_max_iters < 0 ||
+                   tuning->long_len < 0))
+        return HS_EINVAL;
+    const int warps = tuning ? tuning->warps : 0;
+    const int32_t long_len = tuning && tuning->long_len > 0 ? tuning->long_len : kLongLen;
     const int32_t nhits = (int32_t)std::min<int64_t>(k, db->n);
     if (nhits > 0 && nq > 0 && (!d_hits || !d_ops_used || (ops_cap > 0 && !d_ops))) return HS_EINVAL;
     if (((uintptr_t)d_workspace & 255) != 0) return HS_EINVAL;
@@ -672,6 +678,8 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     if (rc != HS_OK) return rc;
     if (p->mode != HS_MODE_DB) return HS_EINVAL;    // the batched scan is the database-search form
     kp.s.index_base = db->index_base;
+    if (tuning && tuning->flat_min_chunks > 0) kp.s.flat_min_chunks = tuning->flat_min_chunks;
+    if (tuning && tuning->flat_max_iters > 0) kp.s.flat_max_iters = tuning->flat_max_iters;
     bl.queries = d_queries;
     bl.qoffsets = d_qoffsets;
     bl.seeds = d_seeds;
@@ -685,7 +693,7 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
 
     const auto &L = db->sorted_len;
     const int64_t long_end = db->schedule == HS_SCHEDULE_INPUT ? 0 :
-        std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
+        std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= long_len; }) - L.begin();
     DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
     ScanTrace tr{nullptr, nullptr};
     if (db->trace) {
@@ -696,7 +704,7 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     e = launch_prof_offsets(bl, st);
     launches++;
     if (e == cudaSuccess)
-        e = launch_scan_batch(v, db->d_cumres, long_end, kp, bl, nchunk, ctas_per_sm, db->num_sms, d_status, st,
+        e = launch_scan_batch(v, db->d_cumres, long_end, kp, bl, nchunk, warps, db->num_sms, d_status, st,
                               db->trace ? &tr : nullptr, &launches, db->schedule == HS_SCHEDULE_INPUT);
     if (e == cudaSuccess && nhits > 0) e = launch_topk_batch(bl, db->n, k, nhits, st, &launches);
     if (e == cudaSuccess && nhits > 0)

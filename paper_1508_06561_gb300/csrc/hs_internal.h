@@ -37,7 +37,11 @@ struct SParams {
     int32_t mode;                       // HS_MODE_DB or HS_MODE_FULL
     int32_t pair16;                     // 16-bit chunk sums suffice: (max-min) * (qlen+3) <= 65535
     int32_t pack_shifts;                // cell counts also carry the shifts scanned, << 40 (profiling)
+    int32_t flat_min_chunks;            // a step joins the flat unit list with at least this many 4-shift
+    int32_t flat_max_iters;             // chunks, or at most this many iterations per chunk (else lane grid)
 };
+constexpr int kFlatMinChunks = 16;      // defaults of the two (a tuning may change them)
+constexpr int kFlatMaxIters = 128;
 
 // The matrix (for building profiles) plus the scoring parameters.
 struct KParams {
@@ -127,7 +131,7 @@ cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32
                               int *launches);
 cudaError_t launch_prof_offsets(const BatchLayout &bl, cudaStream_t st);
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
-                              const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
+                              const BatchLayout &bl, int32_t nchunk, int warps, int num_sms,
                               int32_t *d_status, cudaStream_t st, const ScanTrace *trace, int *launches,
                               bool input_order);
 cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const BatchLayout &bl, int32_t nhits,

@@ -70,10 +70,8 @@ __global__ void profile_kernel(ProfileJob job, KParams kp)
 // ---------------------------------------------------------------------------
 constexpr int kLocalIters = 64;
 // flattened scan (16-bit pair sums): a step joins the unit list when it has
-// at least kFlatMinChunks chunks or at most kFlatMaxIters iterations per
-// chunk; the rest (few long chunks) get the warp's lane grid
-constexpr int kFlatMinChunks = 16;
-constexpr int kFlatMaxIters = 128;
+// at least sp.flat_min_chunks chunks or at most sp.flat_max_iters iterations
+// per chunk; the rest (few long chunks) get the warp's lane grid
 
 struct QueryCtx {
     const uint32_t *prof_rev;       // profile for pairs where the query is the small sequence
@@ -226,7 +224,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             const int32_t nchunk = (ls - g.ss + 4) >> 2;
             const int32_t niter = g.ss + (L.qsmall ? 3 : 0);
             if constexpr (P16) {
-                flat = ls - g.ss < 65536 && (nchunk >= kFlatMinChunks || niter <= kFlatMaxIters);
+                flat = ls - g.ss < 65536 && (nchunk >= sp.flat_min_chunks || niter <= sp.flat_max_iters);
                 if (!flat) plan_grid(g);
             } else {
                 local = (int64_t)nchunk * niter <= kLocalIters;
@@ -765,7 +763,7 @@ __global__ void batch_classes_kernel(const int64_t *qoffsets, int32_t nq, int32_
 }
 
 cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t long_end, const KParams &kp,
-                              const BatchLayout &bl, int32_t nchunk, int ctas_per_sm, int num_sms,
+                              const BatchLayout &bl, int32_t nchunk, int warps, int num_sms,
                               int32_t *d_status, cudaStream_t st, const ScanTrace *trace, int *launches,
                               bool input_order)
 {
@@ -805,8 +803,10 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         bs.item_ctr = bl.item_ctrs + c;
         bs.smem_words = input_order ? 0 : profile_words(cls_len);
         size_t smem = (size_t)bs.smem_words * 4;
-        // the long class: the widest CTA that fits its profile and slots
-        const int wide = !input_order ? wide_warps(bs.smem_words) : 0;
+        // the widest CTA that fits the class's profile and slots, or the
+        // tuning's choice of 24 or 12 warps when that fits
+        int wide = !input_order ? wide_warps(bs.smem_words) : 0;
+        if (wide && (warps == 12 || warps == 24) && warps < wide) wide = warps;
         bs.chunk_step = wide ? (wide + kWarpsPerCta - 1) / kWarpsPerCta : 1;
         const BatchKernelFn kc = wide ? pick_batch_wide_kernel(wide, kp.s.pair16 != 0) : kern;
         if (wide) smem += wide * kWarpSlotBytes;
@@ -815,7 +815,6 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
         e = launch_fit(reinterpret_cast<const void *>(kc), threads, smem, &per_sm);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        if (ctas_per_sm > 0) per_sm = min(per_sm, ctas_per_sm);
         kc<<<per_sm * num_sms, threads, smem, st>>>(db, bs, kp.s);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -103,6 +103,8 @@ int main(int argc, char **argv)
     int32_t max_qlen = 0;
     for (int q = 0; q < nq; q++) max_qlen = std::max<int32_t>(max_qlen, (int32_t)(qoffsets[q + 1] - qoffsets[q]));
     SParams sp = {};
+    sp.flat_min_chunks = kFlatMinChunks;
+    sp.flat_max_iters = kFlatMaxIters;
     sp.bias = -lo;
     const int range = hi - lo;
     sp.flush = range == 0 ? 255 : std::max(1, 255 / range);

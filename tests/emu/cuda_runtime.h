@@ -29,6 +29,7 @@
 #define __shared__ static
 typedef int cudaError_t;
 struct uint4 { unsigned x, y, z, w; };
+struct alignas(8) uint2 { unsigned x, y; };
 struct int2 { int x, y; };
 inline int2 make_int2(int x, int y) { return int2{x, y}; }
 typedef void *cudaStream_t;

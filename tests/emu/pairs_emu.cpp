@@ -238,6 +238,10 @@ int main(int argc, char **argv)
     int lo = 127, hi = -128;
     for (int i = 0; i < kNSym * kNSym; i++) { lo = std::min<int>(lo, M[i]); hi = std::max<int>(hi, M[i]); }
     SParams sp = {};
+    // the flat-list thresholds (a batched search's tuning may change them)
+    const char *fmin = getenv("HS_EMU_FLAT_MIN_CHUNKS"), *fmax = getenv("HS_EMU_FLAT_MAX_ITERS");
+    sp.flat_min_chunks = fmin ? atoi(fmin) : kFlatMinChunks;
+    sp.flat_max_iters = fmax ? atoi(fmax) : kFlatMaxIters;
     sp.bias = -lo;
     const int range = hi - lo;
     sp.flush = range == 0 ? 255 : std::max(1, 255 / range);

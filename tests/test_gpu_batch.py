@@ -28,7 +28,10 @@ def uneven_queries(rng, n):
     return [synth.residues(rng, int(L)) for L in lens[:n]]
 
 
-@pytest.mark.parametrize("tuning", [None, {"chunks": 1}, {"chunks": 7, "ctas_per_sm": 1}, {"chunks": 8192}])
+@pytest.mark.parametrize("tuning", [None, {"chunks": 1}, {"chunks": 7, "warps": 12}, {"chunks": 8192},
+                                    {"flat_min_chunks": 1, "flat_max_iters": 1},
+                                    {"flat_min_chunks": 100000, "flat_max_iters": 100000, "long_len": 1},
+                                    {"warps": 12, "flat_min_chunks": 64, "flat_max_iters": 32, "long_len": 8192}])
 def test_batch_equals_plain_per_query(tuning):
     rng = np.random.default_rng(77)
     lengths = np.concatenate([synth.lognormal_lengths(rng, 4000, 300, 0.6, 1, 4000), [0, 1, 6000, 2500]])

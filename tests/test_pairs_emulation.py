@@ -60,7 +60,7 @@ def emu(tmp_path_factory):
     return exe, d
 
 
-def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how=""):
+def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", flat=None):
     exe, d = emu
     n = len(offsets) - 1
     hdr = struct.pack("<qqiiiiiiiIIIQq", n, len(codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds, p.mode,
@@ -72,7 +72,10 @@ def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how=""):
         f.write(np.ascontiguousarray(codes, np.uint8).tobytes())
         f.write(np.ascontiguousarray(offsets, np.int64).tobytes())
         f.write(np.ascontiguousarray(q, np.uint8).tobytes())
-    subprocess.run([exe, inp, out] + ([how] if how else []), check=True, timeout=600)
+    env = dict(os.environ)
+    if flat is not None:            # (flat_min_chunks, flat_max_iters), as a batch tuning sets them
+        env["HS_EMU_FLAT_MIN_CHUNKS"], env["HS_EMU_FLAT_MAX_ITERS"] = str(flat[0]), str(flat[1])
+    subprocess.run([exe, inp, out] + ([how] if how else []), check=True, timeout=600, env=env)
     with open(out, "rb") as f:
         b = f.read()
     scores = np.frombuffer(b, np.int32, n)
@@ -99,8 +102,8 @@ def mixed_db(rng, n_short, long_lens, extra=(0, 1, 2, 3)):
     return synth.db_from_lengths(rng, lengths)
 
 
-def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, how=""):
-    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how)
+def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, how="", flat=None):
+    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how, flat)
     ref, refc = oracle_scores(db, q, M, p, seed, index_base)
     bad = np.nonzero(s != ref)[0]
     assert bad.size == 0, "scores differ at %s: %s vs oracle %s" % (bad[:5], s[bad[:5]], ref[bad[:5]])
@@ -277,7 +280,9 @@ def test_shared_memory_traffic_is_ordered(emu_tsan, how):
 def test_random_configurations(emu, case):
     """Seeded random databases, queries, matrices and parameters: lengths
     around the role switch and the one-per-warp threshold, matrix ranges
-    from 1 to 255, every factor and penalty in its accepted range."""
+    from 1 to 255, every factor and penalty in its accepted range, and in
+    two cases of three random flat-list thresholds (every step flat, every
+    step on the lane grid, and between)."""
     rng = np.random.default_rng(1000 + case)
     qlen = int(rng.choice([1, 2, 5, 31, 64, 129, 256, 511, 1000]))
     lengths = np.concatenate([rng.integers(0, 2 * qlen + 8, 40), [qlen - 1, qlen, qlen + 1],
@@ -289,4 +294,6 @@ def test_random_configurations(emu, case):
     p = O.paper_params(pgp=int(rng.integers(0, 6)), gop=int(rng.integers(0, 20)), gep=int(rng.integers(0, 8)),
                        rounds=int(rng.integers(1, 4)), lfactor_q16=int(rng.integers(0, 65537)),
                        sfactor_q16=int(rng.integers(0, 65537)), minfactor_q16=int(rng.integers(0, 65537)))
-    check(emu, db, synth.residues(rng, qlen), M, p, int(rng.integers(0, 2**63)), warps=int(rng.integers(1, 4)))
+    flat = None if case % 3 == 0 else (int(rng.choice([1, 4, 16, 64, 100000])), int(rng.choice([1, 32, 128, 100000])))
+    check(emu, db, synth.residues(rng, qlen), M, p, int(rng.integers(0, 2**63)), warps=int(rng.integers(1, 4)),
+          flat=flat)
