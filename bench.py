@@ -328,11 +328,14 @@ def serving_section(P, D, db, params, seconds, rates=(50.0, 200.0, 1000.0)):
             h0, o0 = P.search(D, qs[i], 100, params, int(seeds[i]))
             same &= bool(np.array_equal(res[i][0], h0) and np.array_equal(res[i][1], o0))
         lat = serve.latency_stats(srv.latencies)
+        ov = serve.overlap_stats(srv.intervals)
         nb = [b for b, _ in srv.batches]
         out["rates"].append({"offered_req_s": rate, "requests": n, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
                              "mean_ms": lat["mean_ms"], "served_req_s": n / (t_end - t0),
                              "residues_per_s": n * db.residues / (t_end - t0), "batches": len(nb),
                              "mean_batch": float(np.mean(nb)), "max_batch": int(np.max(nb)),
+                             "device_busy_frac": ov["device_busy_ms"] / 1000.0 / (t_end - t0),
+                             "batches_overlapping_frac": ov["overlap_frac"], "max_batches_in_flight": ov["max_in_flight"],
                              "alone_equals_mix": same})
     return out
 
@@ -456,6 +459,43 @@ def small_section(P, params, seed, steps=2000):
             "timing": "CUDA graph of %d searches replayed %d times, CUDA events" % (per_graph, reps),
             "e2e": {"value": n_e2e * db.residues / te, "unit": UNIT, "ms_per_search": te * 1000.0 / n_e2e},
             "l2": "database fits in L2; steps run warm"}
+
+
+# --------------------------------------------------------------------------
+# full-slide pair-wise mode (Fig. 1 as printed, Rounds = 20 as the paper
+# runs it for alignment quality) on the small database: 64-residue query,
+# 2,000 targets, top-10
+# --------------------------------------------------------------------------
+def full_section(P, seed, steps=20):
+    import torch
+
+    from paper_1508_06561_gb300 import synth
+    db, q, k = synth.plain_small(0)
+    D = P.Database(db.codes, db.offsets)
+    params = P.Params(mode=1, rounds=20)
+    st = torch.cuda.Stream()
+    qd = torch.from_numpy(q).cuda()
+    with torch.cuda.stream(st):
+        cnt = P.search_device(D, qd, k, params, seed=seed, stream=st, want_cells=True)
+    st.synchronize()
+    cells = int(cnt["cells"][: D.n].sum().item())
+    with torch.cuda.stream(st):
+        out = P.search_device(D, qd, k, params, seed=seed, stream=st)
+        for _ in range(3):
+            P.search_device(D, qd, k, params, seed=seed, stream=st, workspace=out["workspace"], out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(steps):
+            P.search_device(D, qd, k, params, seed=seed, stream=st, workspace=out["workspace"], out=out)
+        b.record(st)
+    st.synchronize()
+    assert int(out["status"].item()) == 0
+    t = a.elapsed_time(b) / 1000.0 / steps
+    D.close()
+    return {"workload": "full-slide-rounds20-q64-2k", "mode": "full slide (Fig. 1), Rounds = 20", "n_seqs": int(db.n),
+            "residues": int(db.residues), "qlen": int(len(q)), "k": int(k), "value": db.residues / t, "unit": UNIT,
+            "ms_per_search": t * 1000.0, "pairs_per_s": db.n / t, "cells_per_search": cells,
+            "cells_per_s": cells / t}
 
 
 # --------------------------------------------------------------------------
@@ -617,6 +657,7 @@ def run_ours(args, world, rank, local):
     bimodal = bimodal_section(P) if (world == 1 and not args.no_bimodal and args.workload == "plain-large") else None
     small = small_section(P, params, args.seed) if (world == 1 and not args.no_small
                                                      and args.workload == "plain-large") else None
+    full = full_section(P, args.seed) if (world == 1 and not args.no_small and args.workload == "plain-large") else None
     cpu_rate, cpu_threads, ns, nres, tcpu = oracle_rate(db, q, args.seed, args.cpu_budget_s) \
         if world == 1 else (None, None, 0, 0, 0.0)
     line = {
@@ -647,6 +688,8 @@ def run_ours(args, world, rank, local):
         line["bimodal"] = bimodal
     if small is not None:
         line["plain_small"] = small
+    if full is not None:
+        line["full_slide"] = full
     if cpu_rate is not None:
         line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                                 "sample": "%d random sequences (%d residues) of the same database, scores only, "

@@ -162,6 +162,7 @@ __device__ __forceinline__ void fold_keys(FlatSlots *fs, unsigned starts, int ow
 struct PosQueue {
     int64_t begin, long_end, end;
     unsigned *ctr;                  // global or shared counter of handed-out positions
+    unsigned lanes;                 // lanes a warp fills with pairs (bit mask; a small database spreads thin)
 };
 
 template <bool P16>
@@ -179,7 +180,7 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
     for (;;) {
         // refill empty lanes from the queue
         if (open) {
-            unsigned need = __ballot_sync(0xFFFFFFFFu, L.d < 0);
+            unsigned need = __ballot_sync(0xFFFFFFFFu, L.d < 0) & qu.lanes;
             if (phase == 0) need &= 1u;
             if (need) {
                 const int m = __popc(need);
@@ -335,7 +336,18 @@ struct ScanQueue {
     unsigned *ctr;
     int64_t smem_words;             // profile words staged into shared memory
     int rev_off, fwd_off;           // word offsets of the two role profiles
+    unsigned lanes;                 // PosQueue::lanes
 };
+
+// The lanes a warp fills: all 32 when the queue holds at least 32 pairs per
+// resident warp; fewer for a small database, so that its pairs spread over
+// all the warps (a warp's steps still deal their units to all 32 lanes)
+// instead of crowding a few.
+static unsigned lanes_for(int64_t pairs, int64_t warps)
+{
+    const int64_t per = warps > 0 ? (pairs + warps - 1) / warps : 32;
+    return per >= 32 ? 0xFFFFFFFFu : (1u << (unsigned)(per < 1 ? 1 : per)) - 1u;
+}
 
 // The 8-warp scan CTA (static slots, 3 CTAs per SM), used for the
 // database-order schedule; the length-order launches use scan_wide_kernel.
@@ -366,7 +378,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
     qc.prof_fwd = prof + qu.fwd_off;
     qc.scores = scores;
     qc.cells = cells_out;
-    const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
+    const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr, qu.lanes};
     run_pairs<P16>(db, sp, qc, pq, plans[threadIdx.x >> 5], &flat_slots[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
@@ -392,7 +404,7 @@ scan_wide_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, S
     qc.prof_fwd = prof + qu.fwd_off;
     qc.scores = scores;
     qc.cells = cells_out;
-    const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr};
+    const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr, qu.lanes};
     const int w = threadIdx.x >> 5;
     run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, threadIdx.x & 31);
 }
@@ -579,6 +591,7 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         e = launch_fit(reinterpret_cast<const void *>(kern), threads, smem, &per_sm);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        qs[i].lanes = lanes_for(qs[i].end - qs[i].begin, (int64_t)per_sm * num_sms * (threads / 32));
         kern<<<per_sm * num_sms, threads, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores, d_cells);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -696,7 +709,7 @@ __device__ __forceinline__ void batch_items(const DbView &db, const BatchScan &b
                     __syncthreads();
                     qc.prof_rev = prof_w;
                     qc.prof_fwd = prof_w;
-                    const PosQueue pq = {r0, max(r0, min(bs.long_end, r1)), r1, &s_pos};
+                    const PosQueue pq = {r0, max(r0, min(bs.long_end, r1)), r1, &s_pos, 0xFFFFFFFFu};
                     run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, lane);
                     __syncthreads();                        // all warps are done with s_pos
                 }
@@ -704,7 +717,7 @@ __device__ __forceinline__ void batch_items(const DbView &db, const BatchScan &b
                 __syncthreads();
                 qc.prof_rev = pg;
                 qc.prof_fwd = pg + words;
-                const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos};
+                const PosQueue pq = {b0, max(b0, min(bs.long_end, b1)), b1, &s_pos, 0xFFFFFFFFu};
                 run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, lane);
             }
         }

@@ -64,6 +64,9 @@ class _Slot:
         self.h_hits = torch.empty(max_batch * k * HIT_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
         self.h_meta = torch.zeros(2, dtype=torch.int64, pin_memory=True)
         self.event = torch.cuda.Event()
+        # device-time bounds of the batch in flight (for the overlap record)
+        self.ev_start = torch.cuda.Event(enable_timing=True)
+        self.ev_end = torch.cuda.Event(enable_timing=True)
         self.batch = None
 
 
@@ -73,11 +76,18 @@ class Server:
     k: hits per request; params: shared search parameters; max_batch: most
     queries per launch; slots: launches in flight (CUDA streams);
     max_total_qlen: per-slot budget of query letters, which with max_batch
-    and k sizes each slot's device memory (the admission gate)."""
+    and k sizes each slot's device memory (the admission gate); None sizes
+    it from free device memory at start-up: the largest budget whose slot
+    buffers, one per slot, fit `memory_fraction` of the free memory."""
 
     def __init__(self, db: Database, k: int = 100, params: Params | None = None, max_batch: int = 64,
-                 slots: int = 2, max_qlen: int = 2048, max_total_qlen: int = 32768, tuning=None, device=None):
+                 slots: int = 2, max_qlen: int = 2048, max_total_qlen: int | None = 32768, tuning=None, device=None,
+                 memory_fraction: float = 0.5):
         import torch
+        if max_total_qlen is None:
+            dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+            free, _ = torch.cuda.mem_get_info(dev)
+            max_total_qlen = slot_budget(db, k, max_batch, max_qlen, free * memory_fraction / max(slots, 1))
         if max_total_qlen < max_qlen:
             raise ValueError("max_total_qlen (%d) must be at least max_qlen (%d): a request of max_qlen letters "
                              "must fit a batch alone" % (max_total_qlen, max_qlen))
@@ -94,6 +104,9 @@ class Server:
         self.latencies = []                     # seconds from submit to result, per request
         self.errors = []
         self.cancelled = 0                      # requests dropped because their caller cancelled them
+        self.intervals = []                     # (start, end) of every batch on the device, ms from t_ref
+        self.t_ref = torch.cuda.Event(enable_timing=True)
+        self.t_ref.record(torch.cuda.current_stream(self.device))
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -171,6 +184,7 @@ class Server:
         s.h_off[:nq + 1].copy_(torch.from_numpy(off))
         s.h_seed[:nq].copy_(torch.from_numpy(np.array([r.seed for r in batch], dtype=np.uint64).view(np.int64)))
         with torch.cuda.stream(s.stream):
+            s.ev_start.record(s.stream)
             s.d_q[:total].copy_(s.h_q[:total], non_blocking=True)
             s.d_off[:nq + 1].copy_(s.h_off[:nq + 1], non_blocking=True)
             s.d_seed[:nq].copy_(s.h_seed[:nq], non_blocking=True)
@@ -191,6 +205,7 @@ class Server:
             nbytes = nq * self.k * HIT_DTYPE.itemsize
             s.h_hits[:nbytes].copy_(s.d_hits[:nbytes], non_blocking=True)
             s.h_meta.copy_(s.d_meta, non_blocking=True)
+            s.ev_end.record(s.stream)
             s.event.record(s.stream)
         s.batch = (batch, nq, nh)
         self.batches.append((nq, total))
@@ -198,6 +213,12 @@ class Server:
     def _harvest(self, s: _Slot):
         batch = s.batch[0]
         s.batch = None
+        ref = getattr(self, "t_ref", None)
+        if ref is not None:
+            try:
+                self.intervals.append((ref.elapsed_time(s.ev_start), ref.elapsed_time(s.ev_end)))
+            except RuntimeError:            # timing unavailable: the record is informational only
+                pass
         try:
             self._deliver(s, batch)
         except Exception as e:
@@ -262,6 +283,53 @@ class Server:
                 if not progressed:
                     busy = any(s.batch is not None for s in self.slots)
                     self.cv.wait(timeout=0.0002 if busy else 0.01)
+
+
+def slot_bytes(db: Database, k: int, max_batch: int, max_qlen: int, max_total_qlen: int) -> int:
+    """Device bytes one slot holds: the batched workspace, the query,
+    offset and seed buffers, the hits and the ops."""
+    b = C.c_size_t()
+    check(lib().hs_search_batch_workspace_size(db.handle, max_batch, max_total_qlen, max_qlen, k, C.byref(b)),
+          "hs_search_batch_workspace_size")
+    ops = lib().hs_batch_ops_capacity(max_batch, max_total_qlen, k)
+    return int(b.value) + max_total_qlen + 16 * (max_batch + 1) + max_batch * k * HIT_DTYPE.itemsize + 4 * ops + 16
+
+
+def slot_budget(db: Database, k: int, max_batch: int, max_qlen: int, bytes_per_slot: float) -> int:
+    """The largest per-slot letter budget (at least max_qlen, at most
+    max_batch * max_qlen) whose slot fits bytes_per_slot."""
+    lo, hi = max_qlen, max_batch * max_qlen
+    if slot_bytes(db, k, max_batch, max_qlen, lo) > bytes_per_slot:
+        raise MemoryError("one slot for a %d-letter query does not fit the device memory budget" % max_qlen)
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if slot_bytes(db, k, max_batch, max_qlen, mid) <= bytes_per_slot:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+def overlap_stats(intervals_ms):
+    """From the device-time (start, end) of every batch: the time the device
+    had at least one batch in flight, the time it had two or more (batches on
+    different slots overlapping), that fraction, and the most batches in
+    flight at once."""
+    ev = sorted([(a, 1) for a, _ in intervals_ms] + [(b, -1) for _, b in intervals_ms], key=lambda x: (x[0], x[1]))
+    busy = over = 0.0
+    depth = peak = 0
+    last = None
+    for t, d in ev:
+        if last is not None:
+            if depth >= 1:
+                busy += t - last
+            if depth >= 2:
+                over += t - last
+        depth += d
+        peak = max(peak, depth)
+        last = t
+    return {"device_busy_ms": busy, "overlap_ms": over, "overlap_frac": over / busy if busy > 0 else 0.0,
+            "max_in_flight": peak}
 
 
 def latency_stats(requests_latency_s):

@@ -271,7 +271,10 @@ int main(int argc, char **argv)
     qc.prof_fwd = prof_fwd.data();
     qc.scores = scores.data();
     qc.cells = cells.data();
-    const PosQueue pq = {0, long_end, n, &ctr};
+    // lanes a warp fills (the library spreads a small database thin)
+    const char *lanes_env = getenv("HS_EMU_LANES");
+    const int lanes = lanes_env ? atoi(lanes_env) : 32;
+    const PosQueue pq = {0, long_end, n, &ctr, lanes >= 32 ? 0xFFFFFFFFu : (1u << lanes) - 1u};
     if (how == "ops" || how == "ops_cta") {
         std::vector<Replayed> rep((size_t)n);
         run_replay(db, sp, qc, pq, warps, how == "ops_cta", rep);

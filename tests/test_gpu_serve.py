@@ -146,3 +146,23 @@ def test_served_requests_match_oracle_on_the_570k_database():
                 check_hits(dbh, qs[i], M, op, int(seeds[i]), res[i][0], res[i][1], ref, k)
     finally:
         D.close()
+
+
+def test_slots_sized_from_free_device_memory(db):
+    """With no letter budget given, each slot's budget is the largest whose
+    buffers fit the given fraction of free device memory; requests are then
+    admitted against it and served as alone."""
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(db, k=10, max_batch=16, slots=2, max_qlen=512, max_total_qlen=None, memory_fraction=0.02)
+    budget = srv.max_total
+    assert 512 <= budget <= 16 * 512
+    assert serve.slot_bytes(db, 10, 16, 512, budget) <= free * 0.02 / 2
+    rng = np.random.default_rng(6)
+    qs = [synth.residues(rng, int(L)) for L in rng.integers(100, 512, 12)]
+    futs = [srv.submit(q, 40 + i) for i, q in enumerate(qs)]
+    out = [f.result(timeout=120) for f in futs]
+    srv.close()
+    assert all(total <= budget for _, total in srv.batches)
+    for i in (0, 11):
+        h0, o0 = P.search(db, qs[i], 10, seed=40 + i)
+        assert np.array_equal(out[i][0], h0) and np.array_equal(out[i][1], o0)

@@ -60,7 +60,7 @@ def emu(tmp_path_factory):
     return exe, d
 
 
-def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", flat=None):
+def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", flat=None, lanes=None):
     exe, d = emu
     n = len(offsets) - 1
     hdr = struct.pack("<qqiiiiiiiIIIQq", n, len(codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds, p.mode,
@@ -75,6 +75,8 @@ def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", f
     env = dict(os.environ)
     if flat is not None:            # (flat_min_chunks, flat_max_iters), as a batch tuning sets them
         env["HS_EMU_FLAT_MIN_CHUNKS"], env["HS_EMU_FLAT_MAX_ITERS"] = str(flat[0]), str(flat[1])
+    if lanes is not None:           # lanes a warp fills with pairs
+        env["HS_EMU_LANES"] = str(lanes)
     subprocess.run([exe, inp, out] + ([how] if how else []), check=True, timeout=600, env=env)
     with open(out, "rb") as f:
         b = f.read()
@@ -102,8 +104,9 @@ def mixed_db(rng, n_short, long_lens, extra=(0, 1, 2, 3)):
     return synth.db_from_lengths(rng, lengths)
 
 
-def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, how="", flat=None):
-    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how, flat)
+def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, how="", flat=None,
+          lanes=None):
+    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how, flat, lanes)
     ref, refc = oracle_scores(db, q, M, p, seed, index_base)
     bad = np.nonzero(s != ref)[0]
     assert bad.size == 0, "scores differ at %s: %s vs oracle %s" % (bad[:5], s[bad[:5]], ref[bad[:5]])
@@ -297,3 +300,12 @@ def test_random_configurations(emu, case):
     flat = None if case % 3 == 0 else (int(rng.choice([1, 4, 16, 64, 100000])), int(rng.choice([1, 32, 128, 100000])))
     check(emu, db, synth.residues(rng, qlen), M, p, int(rng.integers(0, 2**63)), warps=int(rng.integers(1, 4)),
           flat=flat)
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 17])
+def test_warps_filling_only_some_lanes(emu, lanes):
+    """A small database spreads one or a few pairs per warp: the warp's
+    other lanes hold no pair but still score units of its steps."""
+    rng = np.random.default_rng(60 + lanes)
+    db = mixed_db(rng, 120, [2048, 2100])
+    check(emu, db, synth.residues(rng, 70), O.blosum62(), O.paper_params(rounds=2), 3, warps=3, lanes=lanes)

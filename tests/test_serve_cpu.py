@@ -106,3 +106,12 @@ def test_slot_budget_below_the_longest_request_is_refused():
     import pytest
     with pytest.raises(ValueError):
         serve.Server(None, max_qlen=2048, max_total_qlen=1000)
+
+
+def test_overlap_stats_of_batch_intervals():
+    st = serve.overlap_stats([(0.0, 10.0), (5.0, 12.0), (20.0, 25.0)])
+    assert st["device_busy_ms"] == 17.0 and st["overlap_ms"] == 5.0 and st["max_in_flight"] == 2
+    assert abs(st["overlap_frac"] - 5.0 / 17.0) < 1e-12
+    assert serve.overlap_stats([])["overlap_frac"] == 0.0
+    st = serve.overlap_stats([(0.0, 4.0), (1.0, 2.0), (1.5, 3.0)])
+    assert st["max_in_flight"] == 3 and st["overlap_ms"] == 2.0
