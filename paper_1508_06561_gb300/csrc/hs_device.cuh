@@ -180,12 +180,22 @@ __device__ __forceinline__ void rev_masked(const uint32_t *prof, int R, const ui
 // is small, columns of the reversed query descend; +1: the query is large).
 // Four byte accumulators take a block's iterations in turn (at most flush
 // each from a block of 4 * flush), eight iterations per loop trip so that a
-// trip's letter loads issue together.  Rows are addressed by unsigned byte
-// offsets from pointers bumped once per trip, so an iteration is the letter
-// load, one multiply-add for the row, the shared load with an immediate
-// column offset and the add: 4.3 instructions per iteration measured,
-// against 6.6 with signed word indexing (pw[letter * R - i]).
+// trip's loads issue together.
+//   Rows are addressed by unsigned byte offsets from pointers bumped once
+// per trip (4.3 instructions per iteration measured, against 6.6 with
+// signed word indexing).
+//   The scan is bound by the L1 data pipe's wavefronts (profile loads from
+// shared memory plus letter loads), so the letters come as aligned 32-bit
+// words -- two new words per 8 iterations -- aligned to tp by one funnel
+// shift per 4 letters and split by byte permutes, instead of one byte load
+// per iteration.  Words are read from tp rounded down to 4 bytes up to 11
+// bytes past the last letter, inside the database's read padding.
 __device__ __forceinline__ uint32_t word_at(const char *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ unsigned letter_of(uint32_t quad, int b)
+{
+    return __byte_perm(quad, 0u, 0x4440 + b);       // byte b of quad, zero-extended
+}
 
 template <bool P16, int kDir>
 __device__ __forceinline__ void run_sums(const uint32_t *col0, int R, const uint8_t *tp, int n, int flush,
@@ -194,40 +204,48 @@ __device__ __forceinline__ void run_sums(const uint32_t *col0, int R, const uint
     const char *pb = reinterpret_cast<const char *>(col0);
     const unsigned R4 = 4u * (unsigned)R;
     constexpr int d = 4 * kDir;                     // bytes per iteration along the row
-    for (int c = 0; c < n; c += 4 * flush) {
+    const uintptr_t ta = reinterpret_cast<uintptr_t>(tp);
+    const uint32_t *tw = reinterpret_cast<const uint32_t *>(ta & ~(uintptr_t)3);
+    const unsigned sh = 8u * (unsigned)(ta & 3u);   // letter j sits sh bits into word pair (j/4, j/4 + 1)
+    uint32_t lo = tw[0];
+    for (int c = 0; c < n; c += 4 * flush) {        // blocks of 4 * flush iterations: a multiple of 4
         const int m = min(n - c, 4 * flush);
         uint32_t x = 0, y = 0, z = 0, w = 0;
         int j = 0;
         for (; j + 7 < m; j += 8) {
-            const unsigned a0 = tp[0], a1 = tp[1], a2 = tp[2], a3 = tp[3];
-            const unsigned a4 = tp[4], a5 = tp[5], a6 = tp[6], a7 = tp[7];
-            x += word_at(pb + a0 * R4);
-            y += word_at(pb + a1 * R4 + d);
-            z += word_at(pb + a2 * R4 + 2 * d);
-            w += word_at(pb + a3 * R4 + 3 * d);
-            x += word_at(pb + a4 * R4 + 4 * d);
-            y += word_at(pb + a5 * R4 + 5 * d);
-            z += word_at(pb + a6 * R4 + 6 * d);
-            w += word_at(pb + a7 * R4 + 7 * d);
-            tp += 8;
+            const uint32_t m1 = tw[1], m2 = tw[2];
+            const uint32_t q0 = __funnelshift_r(lo, m1, sh), q1 = __funnelshift_r(m1, m2, sh);
+            x += word_at(pb + letter_of(q0, 0) * R4);
+            y += word_at(pb + letter_of(q0, 1) * R4 + d);
+            z += word_at(pb + letter_of(q0, 2) * R4 + 2 * d);
+            w += word_at(pb + letter_of(q0, 3) * R4 + 3 * d);
+            x += word_at(pb + letter_of(q1, 0) * R4 + 4 * d);
+            y += word_at(pb + letter_of(q1, 1) * R4 + 5 * d);
+            z += word_at(pb + letter_of(q1, 2) * R4 + 6 * d);
+            w += word_at(pb + letter_of(q1, 3) * R4 + 7 * d);
+            lo = m2;
+            tw += 2;
             pb += 8 * d;
         }
         if (j + 3 < m) {
-            const unsigned a0 = tp[0], a1 = tp[1], a2 = tp[2], a3 = tp[3];
-            x += word_at(pb + a0 * R4);
-            y += word_at(pb + a1 * R4 + d);
-            z += word_at(pb + a2 * R4 + 2 * d);
-            w += word_at(pb + a3 * R4 + 3 * d);
-            tp += 4;
+            const uint32_t m1 = tw[1];
+            const uint32_t q0 = __funnelshift_r(lo, m1, sh);
+            x += word_at(pb + letter_of(q0, 0) * R4);
+            y += word_at(pb + letter_of(q0, 1) * R4 + d);
+            z += word_at(pb + letter_of(q0, 2) * R4 + 2 * d);
+            w += word_at(pb + letter_of(q0, 3) * R4 + 3 * d);
+            lo = m1;
+            tw += 1;
             pb += 4 * d;
             j += 4;
         }
-        const int r = m - j;                        // 0 .. 3 left
-        if (r > 0) x += word_at(pb + (unsigned)tp[0] * R4);
-        if (r > 1) y += word_at(pb + (unsigned)tp[1] * R4 + d);
-        if (r > 2) z += word_at(pb + (unsigned)tp[2] * R4 + 2 * d);
-        tp += r;
-        pb += r * d;
+        const int r = m - j;                        // 0 .. 3 left, only in the last block
+        if (r > 0) {
+            const uint32_t q0 = __funnelshift_r(lo, tw[1], sh);
+            x += word_at(pb + letter_of(q0, 0) * R4);
+            if (r > 1) y += word_at(pb + letter_of(q0, 1) * R4 + d);
+            if (r > 2) z += word_at(pb + letter_of(q0, 2) * R4 + 2 * d);
+        }
         A.add(x);
         A.add(y);
         A.add(z);

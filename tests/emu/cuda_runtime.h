@@ -14,6 +14,8 @@
 // so a harness runs one CTA at a time.
 #pragma once
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstddef>
 #include <cstring>
 #include <algorithm>
@@ -127,11 +129,33 @@ template <class T, class Op> inline T emu_reduce(T v, Op op) {
         return r;
     });
 }
-inline unsigned __reduce_or_sync(unsigned, unsigned v) { return emu_reduce(v, [](unsigned a, unsigned b) { return a | b; }); }
-inline int __reduce_max_sync(unsigned, int v) { return emu_reduce(v, [](int a, int b) { return std::max(a, b); }); }
-inline unsigned __reduce_max_sync(unsigned, unsigned v) { return emu_reduce(v, [](unsigned a, unsigned b) { return std::max(a, b); }); }
-inline int __reduce_min_sync(unsigned, int v) { return emu_reduce(v, [](int a, int b) { return std::min(a, b); }); }
-inline unsigned __reduce_min_sync(unsigned, unsigned v) { return emu_reduce(v, [](unsigned a, unsigned b) { return std::min(a, b); }); }
+// A reduction over the lanes named in the calling lane's mask.  Every lane
+// of the warp takes part in the exchange; lanes may pass different masks
+// (disjoint groups), but every lane named in a mask must have passed that
+// same mask, as the hardware requires: otherwise the run aborts.
+template <class T, class Op> inline T emu_reduce_masked(unsigned mask, T v, Op op) {
+    static_assert(sizeof(T) == 4, "32-bit reductions");
+    if (!emu_warp) return v;
+    const uint64_t packed = ((uint64_t)mask << 32) | (uint64_t)(uint32_t)emu_put(v);
+    return emu_exchange(packed, [&](const uint64_t *s) {
+        if (!((mask >> emu_lane) & 1u)) { fprintf(stderr, "warp reduce: lane %d outside its mask\n", emu_lane); abort(); }
+        T r{};
+        bool first = true;
+        for (int i = 0; i < 32; i++) {
+            if (!((mask >> i) & 1u)) continue;
+            if ((unsigned)(s[i] >> 32) != mask) { fprintf(stderr, "warp reduce: lanes of one mask disagree\n"); abort(); }
+            const T x = emu_get<T>(s[i] & 0xFFFFFFFFull);
+            r = first ? x : op(r, x);
+            first = false;
+        }
+        return r;
+    });
+}
+inline unsigned __reduce_or_sync(unsigned m, unsigned v) { return emu_reduce_masked(m, v, [](unsigned a, unsigned b) { return a | b; }); }
+inline int __reduce_max_sync(unsigned m, int v) { return emu_reduce_masked(m, v, [](int a, int b) { return std::max(a, b); }); }
+inline unsigned __reduce_max_sync(unsigned m, unsigned v) { return emu_reduce_masked(m, v, [](unsigned a, unsigned b) { return std::max(a, b); }); }
+inline int __reduce_min_sync(unsigned m, int v) { return emu_reduce_masked(m, v, [](int a, int b) { return std::min(a, b); }); }
+inline unsigned __reduce_min_sync(unsigned m, unsigned v) { return emu_reduce_masked(m, v, [](unsigned a, unsigned b) { return std::min(a, b); }); }
 inline int __all_sync(unsigned, int p) { return emu_reduce(p ? 1 : 0, [](int a, int b) { return a & b; }); }
 inline void __syncwarp(unsigned = 0xFFFFFFFFu) { if (emu_warp) emu_warp->sync(); }
 inline unsigned atomicAdd(unsigned *p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
