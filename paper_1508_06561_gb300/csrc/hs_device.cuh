@@ -684,32 +684,126 @@ __device__ __forceinline__ int32_t align_round_cta(const PairCtx &c, const SPara
 // Alignment slides small from overlapping large's first letter with its last
 // letter to overlapping large's last letter with its first: shifts
 // k = -(ss-1) .. ls-1, V(k) summed over the overlap only, lowest k on ties.
-// Lanes take shifts in turn and sum their overlaps cell by cell (byte 0 of a
-// profile word is the cell of its own column).
+//
+// The same 4-shift byte-lane chunks as the database form, from
+// k0 = -(ss-1) in steps of 4; a chunk's iterations are clipped to the
+// overlap and the bytes outside it are masked:
+//   query small (rev): iteration p reads target letter Lp+k0+p, so the
+//     window clips p to [-k0, ls-k0); byte w holds query letter Sp+p-w,
+//     real while 0 <= p-w < ss (masks at p < 3 and p >= ss, as before);
+//   query large (fwd): iteration j reads small letter Sp+j; byte w holds
+//     query column Lp+k0+w+j, inside the window while 0 <= k0+w+j < ls
+//     (masks where k0+j < 0 or k0+j+3 >= ls).
+// Masked bytes add 0 and the others M + bias, so V(k) = sum - bias * (the
+// overlap's length).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void full_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias, int lane,
-                                          int32_t &vmax, int32_t &kstar)
+
+// bytes w with a <= w < b, of 0..3
+__device__ __forceinline__ uint32_t byte_range_mask(int a, int b)
 {
-    const int nshift = g.ls + g.ss - 1;
+    const uint32_t lo = a <= 0 ? 0xFFFFFFFFu : (a >= 4 ? 0u : (0xFFFFFFFFu << (8 * a)));
+    const uint32_t hi = b >= 4 ? 0xFFFFFFFFu : (b <= 0 ? 0u : (0xFFFFFFFFu >> (8 * (4 - b))));
+    return lo & hi;
+}
+
+// iterations i in [i0, i1): row tl[i], word column col0 + kDir * i, bytes
+// [a0 - kDir * i, b0 - kDir * i) kept
+template <bool P16, int kDir>
+__device__ __forceinline__ void masked_sums(const uint32_t *prof, int R, const uint8_t *tl, int col0, int a0, int b0,
+                                            int i0, int i1, int flush, Acc<P16> &A)
+{
+    uint32_t x = 0;
+    int n = 0;
+    for (int i = i0; i < i1; i++) {
+        x += prof[tl[i] * R + col0 + kDir * i] & byte_range_mask(a0 - kDir * i, b0 - kDir * i);
+        if (++n == flush) { A.add(x); x = 0; n = 0; }
+    }
+    A.add(x);
+}
+
+// Segment gj of 2^lgj (contiguous, about equal) of chunk k0's iterations.
+template <bool P16>
+__device__ __forceinline__ void full_chunk(const uint32_t *prof, int R, int qlen, const Plan &g, int k0, int gj,
+                                           int lgj, int flush, Acc<P16> &A)
+{
+    const int ls = g.ls, ss = g.ss;
+    int ia, ib, ca, cb;                 // iterations, and those with every byte real
+    if (g.qsmall) { ia = max(0, -k0); ib = min(ss + 3, ls - k0); ca = 3; cb = ss; }
+    else { ia = max(0, -k0 - 3); ib = min(ss, ls - k0); ca = -k0; cb = ls - k0 - 3; }
+    const int n = ib - ia;
+    const int sa = ia + ((n * gj) >> lgj), sb = ia + ((n * (gj + 1)) >> lgj);
+    const int h = min(max(ca, sa), sb), e = max(min(cb, sb), h);     // [sa, h) masked, [h, e) not, [e, sb) masked
+    if (g.qsmall) {
+        const uint8_t *tl = g.t + g.Lp;                 // iteration p reads tl[k0 + p]
+        const int sbase = qlen + 3 - g.Sp;
+        masked_sums<P16, -1>(prof, R, tl + k0, sbase, 1 - ss, 1, sa, h, flush, A);
+        if (e > h) run_sums<P16, -1>(prof + (sbase - h), R, tl + (k0 + h), e - h, flush, A);
+        masked_sums<P16, -1>(prof, R, tl + k0, sbase, 1 - ss, 1, e, sb, flush, A);
+    } else {
+        const uint8_t *ts = g.t + g.Sp;
+        const int s0 = g.Lp + k0 + 4;
+        masked_sums<P16, 1>(prof, R, ts, s0, -k0, ls - k0, sa, h, flush, A);
+        if (e > h) run_sums<P16, 1>(prof + (s0 + h), R, ts + h, e - h, flush, A);
+        masked_sums<P16, 1>(prof, R, ts, s0, -k0, ls - k0, e, sb, flush, A);
+    }
+}
+
+// overlap length of shift k
+__device__ __forceinline__ int full_overlap(int ls, int ss, int k) { return min(ss, ls - k) - max(0, -k); }
+
+// The whole warp scans one full-slide step: lanes form a Gk x Gj = 32 grid
+// (Gk chunks side by side, each chunk's iterations split into Gj segments
+// whose byte sums are added by shuffles), the shape that takes the fewest
+// iteration times: passes x (iterations per segment + a pass's setup, ~8,
+// and its shuffles), with segments of at least 4 iterations.
+__device__ __forceinline__ int full_grid_lgk(int nchunk, int niter)
+{
+    int best = 5, best_cost = INT_MAX;
+    for (int lk = 5; lk >= 0; lk--) {
+        const int lj = 5 - lk;
+        if (lj > 0 && (niter >> lj) < 4) break;       // segments only get shorter from here
+        const int passes = (nchunk + (1 << lk) - 1) >> lk;
+        const int cost = passes * (((niter + (1 << lj) - 1) >> lj) + 8 + 2 * lj);
+        if (cost < best_cost) { best_cost = cost; best = lk; }
+    }
+    return best;
+}
+
+template <bool P16>
+__device__ __forceinline__ void full_scan_t(const uint32_t *prof, int R, int qlen, const Plan &g, int bias, int flush,
+                                            int lane, int32_t &vmax, int32_t &kstar)
+{
+    const int ls = g.ls, ss = g.ss;
+    const int nchunk = (ls + ss - 1 + 3) >> 2;
+    const int niter = g.qsmall ? ss + 3 : ss;         // the most any chunk has
+    const int lgk = full_grid_lgk(nchunk, niter), lgj = 5 - lgk;
+    const int Gk = 1 << lgk, Gj = 1 << lgj;
+    const int gk = lane >> lgj, gj = lane & (Gj - 1);
     int32_t bv = INT_MIN, bk = INT_MAX;
-    for (int x = lane; x < nshift; x += 32) {
-        const int k = x - (g.ss - 1);
-        const int j0 = max(0, -k), j1 = min(g.ss, g.ls - k);
-        int32_t v = 0;
-        if (g.qsmall) {                 // letter from the target window, reversed query column
-            const uint8_t *tl = g.t + g.Lp + k;
-            const uint32_t *pw = prof + (qlen + 3 - g.Sp);
-            for (int j = j0; j < j1; j++) v += (int32_t)(pw[tl[j] * R - j] & 0xFFu);
-        } else {                        // letter from the target piece, query column
-            const uint8_t *ts = g.t + g.Sp;
-            const uint32_t *pw = prof + (g.Lp + k + 4);
-            for (int j = j0; j < j1; j++) v += (int32_t)(pw[ts[j] * R + j] & 0xFFu);
-        }
-        v -= bias * (j1 - j0);
-        if (v > bv) { bv = v; bk = x; }   // x ascends within a lane: keeps the lowest
+    for (int c0 = 0; c0 < nchunk; c0 += Gk) {
+        const int c = c0 + gk;
+        const int k0 = 4 * c - (ss - 1);
+        const bool live = c < nchunk;
+        Acc<P16> A;
+        A.zero();
+        if (live) full_chunk<P16>(prof, R, qlen, g, k0, gj, lgj, flush, A);
+        for (int o = 1; o < Gj; o <<= 1) A.xor_reduce(o);
+        if (live && gj == 0)
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                const int k = k0 + w;
+                const int32_t v = (int32_t)A.get(w) - bias * full_overlap(ls, ss, k);
+                if (k < ls && v > bv) { bv = v; bk = k; }      // k ascends within a lane: keeps the lowest
+            }
     }
     warp_argmax(bv, bk, vmax, kstar);
-    kstar -= g.ss - 1;
+}
+
+__device__ __forceinline__ void full_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias, int flush,
+                                          bool pair16, int lane, int32_t &vmax, int32_t &kstar)
+{
+    if (pair16) full_scan_t<true>(prof, R, qlen, g, bias, flush, lane, vmax, kstar);
+    else full_scan_t<false>(prof, R, qlen, g, bias, flush, lane, vmax, kstar);
 }
 
 // SCORE (reading A2) kept incrementally over the runs of a growing
@@ -770,7 +864,7 @@ __device__ __forceinline__ int32_t align_round_full(const PairCtx &c, const SPar
         const int32_t ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)Srem));           // F2
         Plan g = {c.t, Lp, Sp, ls, ss, c.qsmall ? 1 : 0, 0, 0, 0};
         int32_t vmax, kstar;
-        full_scan(c.prof, c.S, c.qlen, g, kp.bias, lane, vmax, kstar);
+        full_scan(c.prof, c.S, c.qlen, g, kp.bias, kp.flush, kp.pair16 != 0, lane, vmax, kstar);
         cells += (int64_t)ls * ss;           // every (window letter, piece letter) pair overlaps once
         // F3: leading overhang, overlap, trailing overhang of small
         const int32_t j0 = max(0, -kstar), j1 = min(ss, ls - kstar);

@@ -71,8 +71,10 @@ struct Workspace {
     int32_t topk_ctas;
     int32_t k;
 };
+// kFullItems0/1: 64-bit item counters (two words each) of the full-slide
+// scan's one or two queues, at 8-byte aligned offsets.
 enum Counter { kQsLong = 0, kQsShort = 1, kQlLong = 2, kQlShort = 3, kTopkTicket = 4, kReplayTicket = 5,
-               kNumCounters = 8 };
+               kFullItems0 = 8, kFullItems1 = 10, kNumCounters = 12 };
 
 constexpr int kTopkCtas = 152;
 

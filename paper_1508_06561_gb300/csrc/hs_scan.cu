@@ -23,6 +23,9 @@ struct ProfileJob {
     int32_t qlen;
     uint32_t *prof;
     int32_t *status;              // HS_EINVAL is recorded here for a letter code >= kNSym
+    int32_t *init_scores;         // full-slide mode: [n_init] set to INT_MIN (nullptr: none)
+    int64_t *init_cells;          // full-slide mode: [n_init] set to 0 (nullptr: none)
+    int64_t n_init;
 };
 
 __global__ void profile_kernel(ProfileJob job, KParams kp)
@@ -53,6 +56,12 @@ __global__ void profile_kernel(ProfileJob job, KParams kp)
         const int a = (int)(i / R), s = (int)(i - (int64_t)a * R);
         prof[idx] = profile_word_value(q, qlen, rev, msm, kp.s.bias, a, s);
     }
+    if (job.init_scores)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < job.n_init;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            job.init_scores[i] = INT_MIN;
+            if (job.init_cells) job.init_cells[i] = 0;
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -328,12 +337,58 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
     }
 }
 
+// Full-slide mode (pair-wise form).  A pair's rounds are independent runs of
+// Align (AlignSequences, Fig. 1) whose draws are keyed by (index, round), so
+// a work item is one (position, round): a long pair's rounds run on many
+// warps at once instead of one after another.  Items go out position-major
+// over the length order (the longest pairs' rounds first); each folds its
+// round's score into the pair's by atomicMax (the best of the rounds; the
+// winning round is found again by the replay) and its cells into the
+// pair's count by atomicAdd, so scores must start at INT_MIN and counts at
+// 0 (profile_kernel clears them).
+struct FullQueue {
+    int64_t begin, end;             // positions [begin, end) of the length order
+    unsigned long long *ctr;        // items handed out
+    const uint32_t *prof_rev, *prof_fwd;
+};
+
+__device__ __forceinline__ void run_full_items(const DbView &db, const SParams &sp, const FullQueue &qu,
+                                               int32_t *scores, int64_t *cells_out, int lane)
+{
+    const unsigned long long rounds = (unsigned)sp.rounds;
+    const unsigned long long items = (unsigned long long)(qu.end - qu.begin) * rounds;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(qu.ctr, 1ull);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= items) break;
+        const unsigned long long pi = it / rounds;
+        const int r = (int)(it - pi * rounds);
+        const int64_t d = db.order[qu.begin + (int64_t)pi];
+        const int64_t off = db.offsets[d];
+        PairCtx c;
+        c.t = db.codes + off;
+        c.tlen = (int32_t)(db.offsets[d + 1] - off);
+        c.qlen = sp.qlen;
+        c.qsmall = c.tlen >= sp.qlen;
+        c.prof = c.qsmall ? qu.prof_rev : qu.prof_fwd;
+        c.S = profile_stride(sp.qlen);
+        int64_t cells = 0;
+        const int32_t s = align_round_full<false>(c, sp, (uint64_t)d, r, lane, cells, nullptr, nullptr);
+        if (lane == 0) {
+            atomicMax(&scores[d], s);
+            if (cells_out) atomicAdd(reinterpret_cast<unsigned long long *>(&cells_out[d]), (unsigned long long)cells);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Plain scan: a persistent grid over one queue of the whole database.
 // ---------------------------------------------------------------------------
 struct ScanQueue {
     int64_t begin, long_end, end;
     unsigned *ctr;
+    unsigned long long *items;      // full-slide mode: (position, round) items handed out
     int64_t smem_words;             // profile words staged into shared memory
     int rev_off, fwd_off;           // word offsets of the two role profiles
     unsigned lanes;                 // PosQueue::lanes
@@ -483,8 +538,8 @@ static ScanKernelFn pick_scan_kernel(bool smem, bool p16)
     return p16 ? scan_kernel<false, true> : scan_kernel<false, false>;
 }
 
-// Full-slide mode (pair-wise form): one warp per pair, pairs taken one at a
-// time from the same longest-first queue; the pair's state is warp-uniform.
+// Full-slide mode (pair-wise form): each warp takes (position, round) items
+// (run_full_items) from the queue's 64-bit counter.
 template <bool kSmem>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
@@ -499,28 +554,8 @@ scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, S
         __syncthreads();
         prof = reinterpret_cast<const uint32_t *>(smem_raw);
     }
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        long long pos = 0;
-        if (lane == 0) pos = (long long)qu.begin + (long long)atomicAdd(qu.ctr, 1u);
-        pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
-        if (pos >= qu.end) break;
-        const int64_t d = db.order[pos];
-        const int64_t off = db.offsets[d];
-        PairCtx c;
-        c.t = db.codes + off;
-        c.tlen = (int32_t)(db.offsets[d + 1] - off);
-        c.qlen = sp.qlen;
-        c.qsmall = c.tlen >= sp.qlen;
-        c.prof = prof + (c.qsmall ? qu.rev_off : qu.fwd_off);
-        c.S = profile_stride(sp.qlen);
-        int64_t cells = 0;
-        const int32_t s = align_pair(c, sp, (uint64_t)d, lane, cells, nullptr);
-        if (lane == 0) {
-            scores[d] = s;
-            if (cells_out) cells_out[d] = cells;
-        }
-    }
+    const FullQueue fq = {qu.begin, qu.end, qu.items, prof + qu.rev_off, prof + qu.fwd_off};
+    run_full_items(db, sp, fq, scores, cells_out, threadIdx.x & 31);
 }
 
 size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
@@ -534,6 +569,11 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
 {
     const int64_t words = profile_words(kp.s.qlen);
     ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof, d_status};
+    if (kp.s.mode == HS_MODE_FULL) {
+        job.init_scores = ws.scores;
+        job.init_cells = d_cells;
+        job.n_init = db.n;
+    }
     profile_kernel<<<64, 256, 0, st>>>(job, kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -577,6 +617,7 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < nq; i++) {
+        qs[i].items = reinterpret_cast<unsigned long long *>(ws.counters + (i == 0 ? kFullItems0 : kFullItems1));
         size_t smem = (size_t)qs[i].smem_words * 4;
         const bool staged = qs[i].smem_words > 0;
         // length order: one CTA per SM, the widest whose profile(s) and slots fit
@@ -869,7 +910,6 @@ struct ReplayArgs {
     int64_t ops_cap;
     int64_t *ops_used;
     int32_t *status;
-    int32_t cta_per_hit;            // one CTA per hit (database form, one round, scan scores given)
 };
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
@@ -877,15 +917,20 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
     atomicCAS(status, (int32_t)HS_OK, code);
 }
 
-// kCta: one CTA per hit, one round, database form (only that path is
-// compiled in, which keeps the kernel small); otherwise one warp per hit.
-template <bool kCta>
+// Three forms, each compiled alone (which keeps each kernel small):
+// kReplayWarp, one warp per hit; kReplayStep, one CTA per hit of a one-round
+// database-form search, all its warps scanning each step; kReplayRounds, one
+// CTA per hit of a several-round search, its warps scoring the rounds in
+// turn before warp 0 writes the best one's ops.
+enum ReplayForm { kReplayWarp = 0, kReplayStep = 1, kReplayRounds = 2 };
+
+template <int kForm>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SParams sp0, ReplayArgs ra)
 {
     __shared__ int2 red[kWarpsPerCta];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    constexpr bool cta = kCta;
+    constexpr bool cta = kForm != kReplayWarp;
     const int w = cta ? (int)blockIdx.x : (int)blockIdx.x * kWarpsPerCta + warp;     // hit number over all queries
     const int per = max(ra.nhits, 1);
     const int qi = w / per, i = w - qi * per;
@@ -915,11 +960,35 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
         int32_t best, again;
         if (ra.hit_score && ra.hit_score[slot] < sp.min_score) {
             best = again = ra.hit_score[slot];      // below the reporting threshold: no alignment
-        } else if constexpr (kCta) {
+        } else if constexpr (kForm == kReplayStep) {
             // one round: it is the best one, and the scan's score checks the
             // replay; every warp scans each step, warp 0 writes the ops
             best = ra.hit_score[slot];
             again = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, warp, kWarpsPerCta, red, cells, &ow, &span);
+        } else if constexpr (kForm == kReplayRounds) {
+            // warp w scores rounds w, w + 8, ...; the best (highest score,
+            // then the first round, as AlignSequences keeps it) is run again
+            // by warp 0, writing the ops
+            int32_t wb = INT_MIN;
+            int wr = INT_MAX;
+            for (int r = warp; r < sp.rounds; r += kWarpsPerCta) {
+                const int32_t s = sp.mode == HS_MODE_FULL
+                                      ? align_round_full<false>(c, sp, (uint64_t)d, r, lane, cells, nullptr, nullptr)
+                                      : align_round<false>(c, sp, (uint64_t)d, r, lane, cells, nullptr, nullptr);
+                if (s > wb) { wb = s; wr = r; }             // r ascends: the first best stays
+            }
+            if (lane == 0) red[warp] = make_int2(wb, wr);
+            __syncthreads();
+            best = INT_MIN;
+            br = INT_MAX;
+            for (int x = 0; x < kWarpsPerCta; x++) {
+                const int2 v = red[x];
+                if (v.x > best || (v.x == best && v.y < br)) { best = v.x; br = v.y; }
+            }
+            again = best;
+            if (warp == 0)
+                again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span)
+                                                : align_round<true>(c, sp, (uint64_t)d, br, lane, cells, &ow, &span);
         } else if (ra.hit_score && sp.rounds == 1) {
             best = ra.hit_score[slot];
             again = sp.mode == HS_MODE_FULL ? align_round_full<true>(c, sp, (uint64_t)d, 0, lane, cells, &ow, &span)
@@ -989,6 +1058,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
     }
 }
 
+// One CTA per hit when its rounds or (one round, database form) its steps
+// can be shared by the CTA's warps; one warp per hit otherwise.
+static void launch_replay_form(const DbView &db, const SParams &sp, const ReplayArgs &ra, int64_t total,
+                               cudaStream_t st)
+{
+    if (sp.rounds > 1)
+        replay_kernel<kReplayRounds><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, sp, ra);
+    else if (sp.mode == HS_MODE_DB && ra.hit_score)
+        replay_kernel<kReplayStep><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, sp, ra);
+    else
+        replay_kernel<kReplayWarp><<<(int)((total + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32, 0, st>>>(
+            db, sp, ra);
+}
+
 static ReplayArgs replay_args_single(const uint8_t *d_query, const uint32_t *prof)
 {
     ReplayArgs ra = {};
@@ -1018,9 +1101,7 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
     ra.ops_cap = ops_cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    ra.cta_per_hit = kp.s.mode == HS_MODE_DB && kp.s.rounds == 1;
-    if (ra.cta_per_hit) replay_kernel<true><<<nhits, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
-    else replay_kernel<false><<<(nhits + kWarpsPerCta - 1) / kWarpsPerCta, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    launch_replay_form(db, kp.s, ra, nhits, st);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -1049,9 +1130,7 @@ cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const Batch
     ra.ops_used = d_ops_used;
     ra.status = d_status;
     const int64_t total = (int64_t)bl.nq * nhits;
-    ra.cta_per_hit = kp.s.mode == HS_MODE_DB && kp.s.rounds == 1;
-    if (ra.cta_per_hit) replay_kernel<true><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
-    else replay_kernel<false><<<(int)((total + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    launch_replay_form(db, kp.s, ra, total, st);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -1080,7 +1159,7 @@ cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KP
     ra.ops_cap = cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    replay_kernel<false><<<1, kWarpsPerCta * 32, 0, st>>>(db, kp.s, ra);
+    launch_replay_form(db, kp.s, ra, 1, st);
     return cudaGetLastError();
 }
 

@@ -159,6 +159,12 @@ inline unsigned __reduce_min_sync(unsigned m, unsigned v) { return emu_reduce_ma
 inline int __all_sync(unsigned, int p) { return emu_reduce(p ? 1 : 0, [](int a, int b) { return a & b; }); }
 inline void __syncwarp(unsigned = 0xFFFFFFFFu) { if (emu_warp) emu_warp->sync(); }
 inline unsigned atomicAdd(unsigned *p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned long long atomicAdd(unsigned long long *p, unsigned long long v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline int atomicMax(int *p, int v) {
+    int old = __atomic_load_n(p, __ATOMIC_SEQ_CST);
+    while (old < v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {}
+    return old;
+}
 inline unsigned atomicMin(unsigned *p, unsigned v) {
     unsigned old = __atomic_load_n(p, __ATOMIC_SEQ_CST);
     while (old > v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {}

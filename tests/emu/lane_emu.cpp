@@ -4,7 +4,9 @@
 // segments, and every lane-local step must equal a naive sum of matrix
 // entries, and every profile/target read must stay inside its buffer: the
 // buffers end at PROT_NONE guard pages, so a stray read faults.
-// Also checked: the flattened scan's per-chunk keys (their maximum over a
+// Also checked: the full-slide mode's chunks (every shift of a step, the
+// overhanging ones included, with windows where ss exceeds ls); the
+// flattened scan's per-chunk keys (their maximum over a
 // step's chunks gives the step's best shift), the same keys through a flat
 // step's packed descriptor, and the owners from the pass start masks.
 // Both accumulator forms are checked: 32-bit sums always, 16-bit pair sums
@@ -49,6 +51,20 @@ long check_chunk(const uint32_t *prof, int R, int qlen, const uint8_t *t, int Lp
         if ((int)A.get(x) - bias * ss != V[k0 + x]) return -1 - x;
     return n;
 }
+// full-slide mode (readings F1-F3): chunk k0 of a step's shifts -(ss-1) ..
+// ls-1, its iterations split into 2^lgj segments summed into one
+// accumulator; same return convention as check_chunk
+template <bool P16>
+long check_full_chunk(const uint32_t *prof, int R, int qlen, const Plan &g, int k0, int lgj, int flush, int bias,
+                      const std::vector<int> &Vf) {
+    Acc<P16> A;
+    A.zero();
+    for (int gj = 0; gj < (1 << lgj); gj++) full_chunk<P16>(prof, R, qlen, g, k0, gj, lgj, flush, A);
+    long n = 0;
+    for (int x = 0; x < 4 && k0 + x < g.ls; x++, n++)
+        if ((int)A.get(x) - bias * full_overlap(g.ls, g.ss, k0 + x) != Vf[k0 + x + g.ss - 1]) return -1 - x;
+    return n;
+}
 template <bool P16>
 bool check_lane_scan(const uint32_t *prof, int R, int qlen, const Plan &g, int bias, int flush, int bestv, int bestk) {
     int32_t vm, ks;
@@ -62,7 +78,7 @@ int main(int argc, char **argv) {
     for (int a = 0; a < 24; a++) for (int b = 0; b <= a; b++) { int v = mlo + (int)(rng() % (mhi - mlo + 1)); M[a*24+b] = M[b*24+a] = (int8_t)v; }
     int lo = 127, hi = -128; for (int i = 0; i < 576; i++) { lo = std::min<int>(lo, M[i]); hi = std::max<int>(hi, M[i]); }
     int bias = -lo, flush = hi == lo ? 255 : std::max(1, 255 / (hi - lo));
-    long checks = 0;
+    long checks = 0, full_checks = 0;
     for (int trial = 0; trial < 3000; trial++) {
         int qlen = 1 + rng() % 300;
         int tlen = 1 + rng() % 600;
@@ -113,6 +129,28 @@ int main(int argc, char **argv) {
                             printf("desc_key mismatch trial %d\n", trial); return 1;
                         }
                 }
+                // full-slide windows: ss up to Srem, so it may exceed ls (F2)
+                {
+                    const int fss = 1 + rng() % Srem;
+                    Plan f = {t, Lp, Sp, ls, fss, qsmall ? 1 : 0, 0, 0, 0};
+                    std::vector<int> Vf(ls + fss - 1);
+                    for (int k = -(fss - 1); k < ls; k++) {
+                        int v = 0;
+                        for (int j = std::max(0, -k); j < std::min(fss, ls - k); j++) {
+                            int a = L[Lp + k + j], b = S[Sp + j];
+                            v += qsmall ? M[b * 24 + a] : M[a * 24 + b];
+                        }
+                        Vf[k + fss - 1] = v;
+                    }
+                    for (int k0 = -(fss - 1); k0 < ls; k0 += 4) {
+                        const int lgj = (int)(rng() % 4);
+                        long c = check_full_chunk<false>(prof, R, qlen, f, k0, lgj, flush, bias, Vf);
+                        if (c >= 0 && p16) c = check_full_chunk<true>(prof, R, qlen, f, k0, lgj, flush, bias, Vf);
+                        if (c < 0) { printf("full chunk mismatch trial %d k %ld\n", trial, k0 - 1 - c); return 1; }
+                        checks += c;
+                        full_checks += c;
+                    }
+                }
                 int niter = qsmall ? ss + 3 : ss;
                 for (int k0 = 0; k0 < nshift; k0 += 4) {
                     int nseg = 1 + rng() % 4;
@@ -161,6 +199,6 @@ int main(int argc, char **argv) {
             carry_u0 = last_u0;
         }
     }
-    printf("emu ok: %ld shift sums checked\n", checks);
+    printf("emu ok: %ld shift sums checked (%ld of them full-slide)\n", checks, full_checks);
     return 0;
 }

@@ -60,9 +60,33 @@ static void run(const DbView &db, const SParams &sp, const QueryCtx &qc, const P
     for (auto &t : th) t.join();
 }
 
-// one pair per warp at a time, as the full-slide scan kernel deals them
+// the full-slide scan's (position, round) items, by the kernel's own loop
+static void run_full(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
+{
+    std::fill(qc.scores, qc.scores + db.n, INT_MIN);
+    std::fill(qc.cells, qc.cells + db.n, 0);
+    unsigned long long ctr = 0;
+    const FullQueue fq = {pq.begin, pq.end, &ctr, qc.prof_rev, qc.prof_fwd};
+    std::vector<EmuWarp> ws(warps);
+    std::vector<std::thread> th;
+    for (int w = 0; w < warps; w++)
+        for (int lane = 0; lane < 32; lane++)
+            th.emplace_back([&, w, lane] {
+                emu_warp = &ws[w];
+                emu_lane = lane;
+                run_full_items(db, sp, fq, qc.scores, qc.cells, lane);
+            });
+    for (auto &t : th) t.join();
+}
+
+// one pair per warp at a time (align_pair: the path of the one-warp replay
+// and hs_get_alignment)
 static void run_whole(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
 {
+    if (sp.mode == HS_MODE_FULL) {
+        run_full(db, sp, qc, pq, warps);
+        return;
+    }
     std::vector<EmuWarp> ws(warps);
     std::vector<std::thread> th;
     for (int w = 0; w < warps; w++)

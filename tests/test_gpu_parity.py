@@ -179,19 +179,22 @@ def oparams_full(p: P.Params):
     return op
 
 
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(7))
 def test_full_slide_mode(case):
     """Fig. 1 as printed (pair-wise form): every score, cell count, ranked
-    hit and alignment equals the oracle's, overhanging pieces included."""
+    hit and alignment equals the oracle's, overhanging pieces included;
+    the last case takes the full int8 matrix range (byte sums widened every
+    cell)."""
     rng = np.random.default_rng(4200 + case)
-    qlen = [1, 7, 40, 130, 300, 700][case]
+    qlen = [1, 7, 40, 130, 300, 700, 90][case]
     lengths = np.concatenate([rng.integers(0, 4, 5), synth.lognormal_lengths(rng, 250, 150, 0.7, 1, 2500)])
     db = synth.db_from_lengths(rng, lengths)
     q = synth.residues(rng, qlen)
     p = P.Params(pgp=int(rng.integers(0, 3)), gop=int(rng.integers(1, 15)), gep=int(rng.integers(0, 6)),
-                 rounds=[1, 20, 3, 20, 2, 5][case], lfactor_q16=int(rng.integers(20000, 65537)),
+                 rounds=[1, 20, 3, 20, 2, 5, 4][case], lfactor_q16=int(rng.integers(20000, 65537)),
                  sfactor_q16=int(rng.integers(20000, 65537)), minfactor_q16=int(rng.integers(0, 40000)),
-                 matrix=None if case % 2 else synth.random_symmetric_matrix(rng, -7, 9))
+                 matrix=synth.random_symmetric_matrix(rng, -128, 127) if case == 6 else
+                 None if case % 2 else synth.random_symmetric_matrix(rng, -7, 9))
     M = O.blosum62() if p.matrix is None else p.matrix
     op = oparams_full(p)
     seed = int(rng.integers(0, 2**62))

@@ -164,9 +164,10 @@ def test_shard_offset_keys_the_draws(emu):
 
 @pytest.mark.parametrize("mode", ["db", "full"])
 def test_one_warp_per_pair(emu, mode):
-    """align_pair, one warp per pair: the full-slide mode's scan (readings
-    F1-F4, several rounds) and the database-mode path the replay and
-    hs_get_alignment run."""
+    """The full-slide scan's loop (run_full_items: one (pair, round) item per
+    warp, rounds folded by atomics; readings F1-F4, several rounds) and, in
+    database mode, align_pair one warp per pair, the path the one-warp replay
+    and hs_get_alignment run."""
     rng = np.random.default_rng(15 if mode == "db" else 16)
     db = mixed_db(rng, 80, [2200])
     if mode == "db":
@@ -174,6 +175,20 @@ def test_one_warp_per_pair(emu, mode):
     else:
         p = O.paper_params(rounds=4, mode=O.MODE_FULL, sfactor_q16=65536, lfactor_q16=65536, minfactor_q16=16384)
     check(emu, db, synth.residues(rng, 60), O.blosum62(), p, 8, warps=3, how="whole")
+
+
+@pytest.mark.parametrize("matrix,qlen", [("blosum62", 300), ("full-range", 120)])
+def test_full_slide_items_both_roles(emu, matrix, qlen):
+    """Full-slide mode (F1-F4) with the query long enough that many targets
+    are shorter (the query is then the large sequence), high size factors
+    (steps whose piece of small is longer than large's window, so every
+    shift overhangs) and, for the full int8 range, byte sums widened every
+    cell."""
+    rng = np.random.default_rng(19 if matrix == "blosum62" else 20)
+    M = O.blosum62() if matrix == "blosum62" else synth.random_symmetric_matrix(rng, -128, 127)
+    db = mixed_db(rng, 70, [900])
+    p = O.paper_params(rounds=5, mode=O.MODE_FULL, sfactor_q16=65536, lfactor_q16=40000, minfactor_q16=8192)
+    check(emu, db, synth.residues(rng, qlen), M, p, 21, warps=3, how="whole")
 
 
 @pytest.mark.parametrize("matrix", ["blosum62", "full-range"])
