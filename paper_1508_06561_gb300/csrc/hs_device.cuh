@@ -706,19 +706,25 @@ __device__ __forceinline__ uint32_t byte_range_mask(int a, int b)
     return lo & hi;
 }
 
-// iterations i in [i0, i1): row tl[i], word column col0 + kDir * i, bytes
-// [a0 - kDir * i, b0 - kDir * i) kept
+// iterations i in [i0, i1), at most 3 of them (a chunk's masked iterations
+// come in runs of at most 3 at either end): row tl[i], word column
+// col0 + kDir * i, bytes [a0 - kDir * i, b0 - kDir * i) kept.  Unrolled and
+// predicated so that the three loads issue together.
 template <bool P16, int kDir>
 __device__ __forceinline__ void masked_sums(const uint32_t *prof, int R, const uint8_t *tl, int col0, int a0, int b0,
                                             int i0, int i1, int flush, Acc<P16> &A)
 {
     uint32_t x = 0;
-    int n = 0;
-    for (int i = i0; i < i1; i++) {
-        x += prof[tl[i] * R + col0 + kDir * i] & byte_range_mask(a0 - kDir * i, b0 - kDir * i);
-        if (++n == flush) { A.add(x); x = 0; n = 0; }
+#pragma unroll
+    for (int u = 0; u < 3; u++) {
+        const int i = i0 + u;
+        if (i < i1) {
+            const uint32_t w = prof[tl[i] * R + col0 + kDir * i] & byte_range_mask(a0 - kDir * i, b0 - kDir * i);
+            if (flush >= 3) x += w;             // three biased bytes fit in a byte lane
+            else A.add(w);
+        }
     }
-    A.add(x);
+    if (flush >= 3) A.add(x);
 }
 
 // Segment gj of 2^lgj (contiguous, about equal) of chunk k0's iterations.

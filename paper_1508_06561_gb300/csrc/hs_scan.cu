@@ -539,9 +539,10 @@ static ScanKernelFn pick_scan_kernel(bool smem, bool p16)
 }
 
 // Full-slide mode (pair-wise form): each warp takes (position, round) items
-// (run_full_items) from the queue's 64-bit counter.
+// (run_full_items) from the queue's 64-bit counter.  Three CTAs per SM (80
+// registers, no spills): the steps' chains of dependent loads want warps.
 template <bool kSmem>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
 scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
                  int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
 {
@@ -920,18 +921,23 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
 // Three forms, each compiled alone (which keeps each kernel small):
 // kReplayWarp, one warp per hit; kReplayStep, one CTA per hit of a one-round
 // database-form search, all its warps scanning each step; kReplayRounds, one
-// CTA per hit of a several-round search, its warps scoring the rounds in
-// turn before warp 0 writes the best one's ops.
+// CTA of 24 warps per hit of a several-round search, its warps scoring the
+// rounds in turn (one each up to 24 rounds) before warp 0 writes the best
+// one's ops.
 enum ReplayForm { kReplayWarp = 0, kReplayStep = 1, kReplayRounds = 2 };
+constexpr int kReplayRoundWarps = 24;
+
+template <int kForm> __host__ __device__ constexpr int replay_warps() { return kForm == kReplayRounds ? kReplayRoundWarps : kWarpsPerCta; }
 
 template <int kForm>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SParams sp0, ReplayArgs ra)
+__global__ void __launch_bounds__(replay_warps<kForm>() * 32) replay_kernel(DbView db, SParams sp0, ReplayArgs ra)
 {
-    __shared__ int2 red[kWarpsPerCta];
+    constexpr int kW = replay_warps<kForm>();
+    __shared__ int2 red[kW];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     constexpr bool cta = kForm != kReplayWarp;
-    const int w = cta ? (int)blockIdx.x : (int)blockIdx.x * kWarpsPerCta + warp;     // hit number over all queries
+    const int w = cta ? (int)blockIdx.x : (int)blockIdx.x * kW + warp;     // hit number over all queries
     const int per = max(ra.nhits, 1);
     const int qi = w / per, i = w - qi * per;
     if (ra.nhits > 0 && qi < ra.nq) {
@@ -964,14 +970,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
             // one round: it is the best one, and the scan's score checks the
             // replay; every warp scans each step, warp 0 writes the ops
             best = ra.hit_score[slot];
-            again = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, warp, kWarpsPerCta, red, cells, &ow, &span);
+            again = align_round_cta<true>(c, sp, (uint64_t)d, 0, lane, warp, kW, red, cells, &ow, &span);
         } else if constexpr (kForm == kReplayRounds) {
-            // warp w scores rounds w, w + 8, ...; the best (highest score,
+            // warp w scores rounds w, w + kW, ...; the best (highest score,
             // then the first round, as AlignSequences keeps it) is run again
             // by warp 0, writing the ops
             int32_t wb = INT_MIN;
             int wr = INT_MAX;
-            for (int r = warp; r < sp.rounds; r += kWarpsPerCta) {
+            for (int r = warp; r < sp.rounds; r += kW) {
                 const int32_t s = sp.mode == HS_MODE_FULL
                                       ? align_round_full<false>(c, sp, (uint64_t)d, r, lane, cells, nullptr, nullptr)
                                       : align_round<false>(c, sp, (uint64_t)d, r, lane, cells, nullptr, nullptr);
@@ -981,7 +987,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
             __syncthreads();
             best = INT_MIN;
             br = INT_MAX;
-            for (int x = 0; x < kWarpsPerCta; x++) {
+            for (int x = 0; x < kW; x++) {
                 const int2 v = red[x];
                 if (v.x > best || (v.x == best && v.y < br)) { best = v.x; br = v.y; }
             }
@@ -1048,7 +1054,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) replay_kernel(DbView db, SP
         }
     }
     __syncthreads();
-    for (int j = warp; j < total_hits; j += kWarpsPerCta) {
+    for (int j = warp; j < total_hits; j += kW) {
         const int slot = (j / ra.nhits) * ra.k + j % ra.nhits;
         const int64_t o = ((volatile int64_t *)&ra.hits[slot].ops_offset)[0];
         const int32_t n = ((volatile int32_t *)ra.slot_len)[slot];
@@ -1064,7 +1070,7 @@ static void launch_replay_form(const DbView &db, const SParams &sp, const Replay
                                cudaStream_t st)
 {
     if (sp.rounds > 1)
-        replay_kernel<kReplayRounds><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, sp, ra);
+        replay_kernel<kReplayRounds><<<(int)total, kReplayRoundWarps * 32, 0, st>>>(db, sp, ra);
     else if (sp.mode == HS_MODE_DB && ra.hit_score)
         replay_kernel<kReplayStep><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, sp, ra);
     else
