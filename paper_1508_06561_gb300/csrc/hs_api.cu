@@ -150,6 +150,7 @@ static int make_kparams(const hs_params *p, int32_t qlen, uint64_t seed, KParams
     sp.pack_shifts = 0;
     sp.flat_min_chunks = kFlatMinChunks;
     sp.flat_max_iters = kFlatMaxIters;
+    sp.help_min_units = kHelpMinUnits;
     return HS_OK;
 }
 
@@ -417,6 +418,11 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
         std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= qlen; }) - L.begin();
     const int64_t long_end = input_order ? 0 :
         std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kLongLen; }) - L.begin();
+    // At least one target of kHelpLen letters per SM: some pair's chain of
+    // steps may outlast the rest of the scan, so idle warps help it (the
+    // plain swissprot-like database has 44 such targets, the bimodal one 8,999).
+    const bool share_steps = !input_order &&
+        std::partition_point(L.begin(), L.end(), [&](int32_t x) { return x >= kHelpLen; }) - L.begin() >= db->num_sms;
     DbView v{db->d_codes, db->d_offsets, db->d_order, db->n};
     ScanTrace tr{nullptr, nullptr};
     if (db->trace) {
@@ -427,7 +433,7 @@ static int run_search(const hs_db *db, const uint8_t *d_query, int32_t qlen, con
     {
         NvtxRange r("hs.scan");
         e = launch_scan(v, split, long_end, d_query, kp, ws, d_cells, d_status, db->num_sms, st,
-                        db->trace ? &tr : nullptr, &launches, input_order);
+                        db->trace ? &tr : nullptr, &launches, input_order, share_steps);
         if (e == cudaSuccess && d_count)
             e = launch_count_at_least(ws.scores, db->n, min_score, d_count, db->num_sms, st, &launches);
     }

@@ -39,9 +39,12 @@ struct SParams {
     int32_t pack_shifts;                // cell counts also carry the shifts scanned, << 40 (profiling)
     int32_t flat_min_chunks;            // a step joins the flat unit list with at least this many 4-shift
     int32_t flat_max_iters;             // chunks, or at most this many iterations per chunk (else lane grid)
-};
+    int32_t help_min_units;             // a warp's lone flat step of at least this many units is shared
+};                                      // with its CTA's idle warps (the scan_wide_kernel launches)
 constexpr int kFlatMinChunks = 16;      // defaults of the two (a tuning may change them)
 constexpr int kFlatMaxIters = 128;
+constexpr int kHelpMinUnits = 256;
+constexpr int kHelpLen = 8192;
 
 // The matrix (for building profiles) plus the scoring parameters.
 struct KParams {
@@ -121,12 +124,16 @@ int64_t slot_stride_for(int32_t qlen);
 // long_end: sorted positions [0, long_end) hold targets of >= kLongLen letters.
 // trace (optional): events recorded around the scan launch(es).
 // launches (optional): incremented by the number of kernels launched.
+// share_steps: the wide scan's warps share large lone steps at the scan's
+// end (the caller sets it for databases with at least one target of
+// kHelpLen letters or more per SM).
 struct ScanTrace {
     cudaEvent_t start, stop;
 };
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int32_t *d_status, int num_sms,
-                        cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order);
+                        cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order,
+                        bool share_steps);
 size_t scan_smem_bytes(int32_t qlen);
 cudaError_t launch_topk(const Workspace &ws, int64_t n, int32_t k, cudaStream_t st, int *launches);
 cudaError_t launch_topk_batch(const BatchLayout &bl, int64_t n, int32_t k, int32_t nhits, cudaStream_t st,

@@ -143,6 +143,20 @@ __device__ __forceinline__ void lane_settle(Lane &L, const SParams &sp, const Qu
     }
 }
 
+// A warp's step shared with the idle warps of its CTA (the end of a scan,
+// when one long pair is left on a warp while the others have run out of
+// pairs).  claim = units of the step << 32 | the next unit to hand out;
+// whoever takes a pass of 32 units (the owner or a helper) scores it, folds
+// its best key into `key` and then adds its units to `done`.  The owner
+// publishes a step only after the previous one is done, and a helper reads
+// the descriptor only after a claim below the step's units, so the
+// descriptor it reads is that step's.
+struct HelpBoard {
+    unsigned long long claim;
+    uint4 desc;
+    uint32_t key, done;
+};
+
 // Per-warp shared slots of the flattened scan, in rank order: each flat
 // step's descriptor and best key, and each lane's rank.
 struct FlatSlots {
@@ -150,6 +164,132 @@ struct FlatSlots {
     uint32_t key[32];
     int32_t rank[32];
 };
+
+// Sharing between the warps of one CTA: every warp's slots and board (warp
+// w's at slots + w, boards + w), the warps still working on pairs of their
+// own, and the status word a wait that runs out records HS_EINTERNAL in.
+struct Help {
+    FlatSlots *slots;
+    HelpBoard *boards;
+    int nw;
+    unsigned *live;
+    int32_t *status;
+};
+constexpr uint64_t kHelpWaitNs = 2000000000ull;     // 2 s: a helper's wait for work; an owner's for its helpers
+
+__device__ __forceinline__ uint64_t help_now_ns()
+{
+#if defined(__CUDA_ARCH__)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+#elif defined(HS_HOST_EMULATION)
+    return emu_now_ns();
+#else
+    return 0;                       // the device compiler's host pass: never called
+#endif
+}
+
+template <class T> __device__ __forceinline__ T help_load(const T *p)
+{
+#if defined(HS_HOST_EMULATION)
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+#else
+    return *reinterpret_cast<const volatile T *>(p);
+#endif
+}
+
+// One pass of a shared step: units base .. base + 31 of tot, by the calling
+// warp; the pass's best key goes into the board before its units count as done.
+__device__ __forceinline__ void help_pass(HelpBoard &bd, const uint4 &d, unsigned base, unsigned tot,
+                                          const QueryCtx &qc, int R, const SParams &sp, int lane)
+{
+    const unsigned u = base + (unsigned)lane;
+    const uint32_t key = u < tot ? desc_key(qc.prof_rev, qc.prof_fwd, R, d, 4 * (int)u, sp.flush) : 0u;
+    const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, key);
+    if (lane == 0) {
+        atomicMax(&bd.key, m);
+        __threadfence_block();
+        atomicAdd(&bd.done, min(32u, tot - base));
+    }
+}
+
+__device__ __forceinline__ void help_fail(const Help *hp)
+{
+    if (hp->status) atomicCAS(hp->status, (int32_t)HS_OK, (int32_t)HS_EINTERNAL);
+}
+
+// The owner's side: publish the lone flat step (slot 0), take passes like
+// any helper, wait for the passes others took, leave the best key in slot 0.
+__device__ __forceinline__ void share_step(const Help *hp, FlatSlots *fs, unsigned tot, const QueryCtx &qc, int R,
+                                           const SParams &sp, int lane)
+{
+    HelpBoard &bd = hp->boards[fs - hp->slots];
+    const uint4 d = fs->desc[0];
+    if (lane == 0) {
+        bd.desc = d;
+        bd.key = 0u;
+        bd.done = 0u;
+        __threadfence_block();
+        atomicExch(&bd.claim, (unsigned long long)tot << 32);
+    }
+    __syncwarp();
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(&bd.claim, 32ull);
+        c = __shfl_sync(0xFFFFFFFFu, c, 0);
+        if ((unsigned)c >= tot) break;
+        help_pass(bd, d, (unsigned)c, tot, qc, R, sp, lane);
+    }
+    if (lane == 0) {
+        const uint64_t t0 = help_now_ns();
+        while (help_load(&bd.done) < tot) {
+            if (help_now_ns() - t0 > kHelpWaitNs) { help_fail(hp); break; }
+        }
+        __threadfence_block();
+        fs->key[0] = help_load(&bd.key);
+    }
+    __syncwarp();
+}
+
+// A warp out of pairs: take passes of the other warps' shared steps until
+// every warp of the CTA is out of pairs (after which none is published), or
+// until it has found none for kHelpWaitNs.
+__device__ __forceinline__ void help_out(const Help *hp, const QueryCtx &qc, int R, const SParams &sp, int lane)
+{
+    __syncwarp();
+    if (lane == 0) atomicAdd(hp->live, 0xFFFFFFFFu);
+    uint64_t t0 = help_now_ns();
+    unsigned nap = 256;                 // ns between looks, doubled up to 4 us while there is no work
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane < hp->nw) c = help_load(&hp->boards[lane].claim);
+        const unsigned open_boards = __ballot_sync(0xFFFFFFFFu, lane < hp->nw && (unsigned)c < (unsigned)(c >> 32));
+        if (open_boards) {
+            HelpBoard &bd = hp->boards[__ffs((int)open_boards) - 1];
+            unsigned long long x = 0;
+            if (lane == 0) x = atomicAdd(&bd.claim, 32ull);
+            x = __shfl_sync(0xFFFFFFFFu, x, 0);
+            __syncwarp();
+            const unsigned base = (unsigned)x, tot = (unsigned)(x >> 32);
+            if (base < tot) help_pass(bd, bd.desc, base, tot, qc, R, sp, lane);
+            t0 = help_now_ns();
+            nap = 256;
+            continue;
+        }
+        unsigned live = 0;
+        if (lane == 0) live = help_load(hp->live);
+        live = __shfl_sync(0xFFFFFFFFu, live, 0);
+        if (live == 0) break;
+        // helping is optional (an owner takes every pass nobody else
+        // takes), so a helper that has found no work for a while leaves
+        bool late = false;
+        if (lane == 0) late = help_now_ns() - t0 > kHelpWaitNs;
+        if (__shfl_sync(0xFFFFFFFFu, late, 0)) break;
+        __nanosleep(nap);
+        nap = min(2 * nap, 4096u);
+    }
+}
 
 // Fold a pass's unit keys into their steps' keys.  Units of one step sit in
 // adjacent lanes; lanes past the list hold key 0, which no maximum notices.
@@ -174,9 +314,15 @@ struct PosQueue {
     unsigned lanes;                 // lanes a warp fills with pairs (bit mask; a small database spreads thin)
 };
 
-template <bool P16>
+// kHelp: the warps of the CTA share large lone steps at the scan's end (hp
+// set).  It is a separate build of the loop because the sharing code, even
+// unused, costs the 80-register loop about 2% (measured), so the library
+// takes it only for databases with many very long targets, where one pair's
+// chain of steps can outlast the rest of the scan.
+template <bool P16, bool kHelp = false>
 __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, const QueryCtx &qc,
-                                          const PosQueue &qu, Plan *plans, FlatSlots *fs, int lane)
+                                          const PosQueue &qu, Plan *plans, FlatSlots *fs, int lane,
+                                          const Help *hp = nullptr)
 {
     const int R = profile_stride(sp.qlen);
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -217,7 +363,10 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
         }
         __syncwarp();
         const bool busy = L.d >= 0;
-        if (!open && __ballot_sync(0xFFFFFFFFu, busy) == 0) break;
+        if (!open && __ballot_sync(0xFFFFFFFFu, busy) == 0) {
+            if constexpr (P16 && kHelp) help_out(hp, qc, R, sp, lane);      // only flat steps are shared
+            break;
+        }
 
         // plan one step per held pair (Fig. 1's Align: ls and ss, A6)
         Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0};
@@ -286,7 +435,19 @@ __device__ __forceinline__ void run_pairs(const DbView &db, const SParams &sp, c
             // owner of the previous pass plus the beginnings up to its lane.
             const int my_u0 = incl - ru;
             int carry = -1, carry_u0 = 0;           // the last unit's owner and its first unit
-            for (int base = 0; base < total; base += 32) {
+            // a lone large step is shared once some warp of the CTA is out of
+            // pairs (only at the scan's end; until then the owner takes every
+            // pass through the plain loop below)
+            bool share = false;
+            if constexpr (kHelp) {
+                if (total >= sp.help_min_units && __popc(__ballot_sync(0xFFFFFFFFu, flat)) == 1) {
+                    unsigned live = 0;
+                    if (lane == 0) live = help_load(hp->live);
+                    share = __shfl_sync(0xFFFFFFFFu, live, 0) < (unsigned)hp->nw;
+                }
+                if (share) share_step(hp, fs, (unsigned)total, qc, R, sp, lane);
+            }
+            for (int base = 0; base < (share ? 0 : total); base += 32) {
                 const int u = base + lane;
                 const bool valid = u < total;
                 uint32_t key = 0u;
@@ -388,6 +549,7 @@ __device__ __forceinline__ void run_full_items(const DbView &db, const SParams &
 struct ScanQueue {
     int64_t begin, long_end, end;
     unsigned *ctr;
+    int32_t *status;                // HS_EINTERNAL if a wait between warps runs out
     unsigned long long *items;      // full-slide mode: (position, round) items handed out
     int64_t smem_words;             // profile words staged into shared memory
     int rev_off, fwd_off;           // word offsets of the two role profiles
@@ -441,7 +603,7 @@ scan_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParam
 // one CTA per SM with kWarps warps, the plan and flat-step slots in dynamic
 // shared memory after the profile, so that the SM keeps as many warps as the
 // fused short-query launch although the profile takes most of its memory.
-template <bool P16, int kWarps>
+template <bool P16, int kWarps, bool kHelp>
 __global__ void __launch_bounds__(kWarps * 32, 1)
 scan_wide_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
                  int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
@@ -449,11 +611,21 @@ scan_wide_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, S
     extern __shared__ uint4 smem_raw[];
     const int64_t n16 = qu.smem_words / 4;
     const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
-    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
-    __syncthreads();
-    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
     Plan *plans = reinterpret_cast<Plan *>(smem_raw + n16);
     FlatSlots *slots = reinterpret_cast<FlatSlots *>(plans + kWarps * 32);
+    HelpBoard *boards = reinterpret_cast<HelpBoard *>(slots + kWarps);
+    unsigned *live = reinterpret_cast<unsigned *>(boards + kWarps);
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+    if (kHelp) {
+        if (threadIdx.x < kWarps) {
+            boards[threadIdx.x].claim = 0ull;           // no step to share
+            boards[threadIdx.x].done = 0u;
+        }
+        if (threadIdx.x == 0) *live = kWarps;
+    }
+    __syncthreads();
+    const uint32_t *prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    const Help help = {slots, boards, kWarps, live, qu.status};
     QueryCtx qc;
     qc.prof_rev = prof + qu.rev_off;
     qc.prof_fwd = prof + qu.fwd_off;
@@ -461,10 +633,12 @@ scan_wide_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, S
     qc.cells = cells_out;
     const PosQueue pq = {qu.begin, qu.long_end, qu.end, qu.ctr, qu.lanes};
     const int w = threadIdx.x >> 5;
-    run_pairs<P16>(db, sp, qc, pq, plans + 32 * w, slots + w, threadIdx.x & 31);
+    run_pairs<P16, kHelp>(db, sp, qc, pq, plans + 32 * w, slots + w, threadIdx.x & 31, &help);
 }
 
 constexpr size_t kWarpSlotBytes = 32 * sizeof(Plan) + sizeof(FlatSlots);
+constexpr size_t kCtaSlotBytes = 16;                 // the wide kernel's live-warp count
+constexpr size_t kHelpSlotBytes = sizeof(HelpBoard);  // and its warps' boards
 
 typedef void (*ScanKernelFn)(DbView, ScanQueue, const uint32_t *, SParams, int32_t *, int64_t *);
 
@@ -522,14 +696,17 @@ static int wide_warps(int64_t smem_words)
     if (optin <= 0) return 0;
     const size_t prof = (size_t)smem_words * 4;
     for (int w : {24, 12})
-        if (prof + w * kWarpSlotBytes <= (size_t)optin) return w;
+        if (prof + w * (kWarpSlotBytes + kHelpSlotBytes) + kCtaSlotBytes <= (size_t)optin) return w;
     return 0;
 }
 
-static ScanKernelFn pick_wide_kernel(int warps, bool p16)
+// help: the build whose warps share large lone steps (16-bit sums only)
+static ScanKernelFn pick_wide_kernel(int warps, bool p16, bool help)
 {
-    if (warps == 24) return p16 ? scan_wide_kernel<true, 24> : scan_wide_kernel<false, 24>;
-    return p16 ? scan_wide_kernel<true, 12> : scan_wide_kernel<false, 12>;
+    if (warps == 24) return p16 ? (help ? scan_wide_kernel<true, 24, true> : scan_wide_kernel<true, 24, false>)
+                                : scan_wide_kernel<false, 24, false>;
+    return p16 ? (help ? scan_wide_kernel<true, 12, true> : scan_wide_kernel<true, 12, false>)
+               : scan_wide_kernel<false, 12, false>;
 }
 
 static ScanKernelFn pick_scan_kernel(bool smem, bool p16)
@@ -566,7 +743,8 @@ static bool fuse_roles(int32_t qlen) { return 2 * scan_smem_bytes(qlen) <= 100 *
 
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
                         const KParams &kp, const Workspace &ws, int64_t *d_cells, int32_t *d_status, int num_sms,
-                        cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order)
+                        cudaStream_t st, const ScanTrace *trace, int *launches, bool input_order,
+                        bool share_steps)
 {
     const int64_t words = profile_words(kp.s.qlen);
     ProfileJob job = {d_query, nullptr, nullptr, kp.s.qlen, ws.prof, d_status};
@@ -619,15 +797,16 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
     }
     for (int i = 0; i < nq; i++) {
         qs[i].items = reinterpret_cast<unsigned long long *>(ws.counters + (i == 0 ? kFullItems0 : kFullItems1));
+        qs[i].status = d_status;
         size_t smem = (size_t)qs[i].smem_words * 4;
         const bool staged = qs[i].smem_words > 0;
         // length order: one CTA per SM, the widest whose profile(s) and slots fit
         const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order ? wide_warps(qs[i].smem_words) : 0;
         const ScanKernelFn kern = kp.s.mode == HS_MODE_FULL
                                       ? (staged ? scan_full_kernel<true> : scan_full_kernel<false>)
-                                      : wide ? pick_wide_kernel(wide, kp.s.pair16 != 0)
+                                      : wide ? pick_wide_kernel(wide, kp.s.pair16 != 0, share_steps)
                                              : pick_scan_kernel(staged, kp.s.pair16 != 0);
-        if (wide) smem += wide * kWarpSlotBytes;
+        if (wide) smem += wide * (kWarpSlotBytes + kHelpSlotBytes) + kCtaSlotBytes;
         const int threads = (kp.s.mode == HS_MODE_FULL ? kWarpsPerCta : wide ? wide : kScanWarps) * 32;
         int per_sm = 0;
         e = launch_fit(reinterpret_cast<const void *>(kern), threads, smem, &per_sm);

@@ -13,13 +13,16 @@
 // harness sets, and a kernel's __shared__ variables are function statics,
 // so a harness runs one CTA at a time.
 #pragma once
+#define HS_HOST_EMULATION 1
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstddef>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
+#include <thread>
 #include <mutex>
 #define __device__
 #define __host__
@@ -81,6 +84,13 @@ inline thread_local int emu_lane = 0;
 inline thread_local EmuBarrier *emu_cta = nullptr;     // all threads of the emulated CTA
 inline void __syncthreads() { if (emu_cta) emu_cta->sync(); }
 inline void __threadfence() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+inline void __threadfence_block() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+inline void __nanosleep(unsigned) { std::this_thread::yield(); }
+// the device's global nanosecond timer
+inline uint64_t emu_now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+        std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 struct EmuDim3 { unsigned x = 0, y = 0, z = 0; };
 inline thread_local EmuDim3 threadIdx, blockIdx, blockDim, gridDim;
 template <class T> inline T __ldcg(const T *p) { return *p; }
@@ -160,6 +170,11 @@ inline int __all_sync(unsigned, int p) { return emu_reduce(p ? 1 : 0, [](int a, 
 inline void __syncwarp(unsigned = 0xFFFFFFFFu) { if (emu_warp) emu_warp->sync(); }
 inline unsigned atomicAdd(unsigned *p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
 inline unsigned long long atomicAdd(unsigned long long *p, unsigned long long v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline unsigned long long atomicExch(unsigned long long *p, unsigned long long v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
+inline int atomicCAS(int *p, int cmp, int v) {
+    __atomic_compare_exchange_n(p, &cmp, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST);
+    return cmp;
+}
 inline int atomicMax(int *p, int v) {
     int old = __atomic_load_n(p, __ATOMIC_SEQ_CST);
     while (old < v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {}

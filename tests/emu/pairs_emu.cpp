@@ -43,21 +43,29 @@ using namespace hs;
 
 template <class T> static bool rd(FILE *f, T *p, size_t n = 1) { return fread(p, sizeof(T), n, f) == n; }
 
+// the warps form one CTA of the wide kernel: idle warps help with the
+// others' large lone steps (sp.help_min_units; env HS_EMU_HELP_MIN)
+static int32_t g_status = 0;
 template <bool P16>
 static void run(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
 {
     std::vector<EmuWarp> ws(warps);
     std::vector<Plan> plans((size_t)warps * 32);
     std::vector<FlatSlots> slots(warps);
+    std::vector<HelpBoard> boards(warps);
+    unsigned live = (unsigned)warps;
+    const Help help = {slots.data(), boards.data(), warps, &live, &g_status};
     std::vector<std::thread> th;
     for (int w = 0; w < warps; w++)
         for (int lane = 0; lane < 32; lane++)
             th.emplace_back([&, w, lane] {
                 emu_warp = &ws[w];
                 emu_lane = lane;
-                run_pairs<P16>(db, sp, qc, pq, plans.data() + 32 * w, &slots[w], lane);
+                run_pairs<P16, true>(db, sp, qc, pq, plans.data() + 32 * w, &slots[w], lane, &help);
             });
     for (auto &t : th) t.join();
+    // 32-bit sums share no step, so their warps never leave through the helper loop
+    if ((P16 && live != 0) || g_status != 0) { fprintf(stderr, "help: live %u status %d\n", live, g_status); exit(3); }
 }
 
 // the full-slide scan's (position, round) items, by the kernel's own loop
@@ -266,6 +274,8 @@ int main(int argc, char **argv)
     const char *fmin = getenv("HS_EMU_FLAT_MIN_CHUNKS"), *fmax = getenv("HS_EMU_FLAT_MAX_ITERS");
     sp.flat_min_chunks = fmin ? atoi(fmin) : kFlatMinChunks;
     sp.flat_max_iters = fmax ? atoi(fmax) : kFlatMaxIters;
+    const char *hmin = getenv("HS_EMU_HELP_MIN");
+    sp.help_min_units = hmin ? atoi(hmin) : kHelpMinUnits;
     sp.bias = -lo;
     const int range = hi - lo;
     sp.flush = range == 0 ? 255 : std::max(1, 255 / range);

@@ -60,7 +60,8 @@ def emu(tmp_path_factory):
     return exe, d
 
 
-def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", flat=None, lanes=None):
+def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", flat=None, lanes=None,
+            help_min=None):
     exe, d = emu
     n = len(offsets) - 1
     hdr = struct.pack("<qqiiiiiiiIIIQq", n, len(codes), len(q), warps, p.pgp, p.gop, p.gep, p.rounds, p.mode,
@@ -77,6 +78,8 @@ def run_emu(emu, codes, offsets, q, M, p, seed, warps=2, index_base=0, how="", f
         env["HS_EMU_FLAT_MIN_CHUNKS"], env["HS_EMU_FLAT_MAX_ITERS"] = str(flat[0]), str(flat[1])
     if lanes is not None:           # lanes a warp fills with pairs
         env["HS_EMU_LANES"] = str(lanes)
+    if help_min is not None:        # units from which a lone flat step is shared with idle warps
+        env["HS_EMU_HELP_MIN"] = str(help_min)
     subprocess.run([exe, inp, out] + ([how] if how else []), check=True, timeout=600, env=env)
     with open(out, "rb") as f:
         b = f.read()
@@ -105,8 +108,9 @@ def mixed_db(rng, n_short, long_lens, extra=(0, 1, 2, 3)):
 
 
 def check(emu, db, q, M, p, seed, warps=2, index_base=0, want_pair16=None, want_long=None, how="", flat=None,
-          lanes=None):
-    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how, flat, lanes)
+          lanes=None, help_min=None):
+    s, c, pair16, long_end = run_emu(emu, db.codes, db.offsets, q, M, p, seed, warps, index_base, how, flat, lanes,
+                                     help_min)
     ref, refc = oracle_scores(db, q, M, p, seed, index_base)
     bad = np.nonzero(s != ref)[0]
     assert bad.size == 0, "scores differ at %s: %s vs oracle %s" % (bad[:5], s[bad[:5]], ref[bad[:5]])
@@ -269,13 +273,18 @@ def emu_tsan(tmp_path_factory):
     return exe, d
 
 
-@pytest.mark.parametrize("how", ["", "cta", "ops_cta"])
+@pytest.mark.parametrize("how", ["", "help", "cta", "ops_cta"])
 def test_shared_memory_traffic_is_ordered(emu_tsan, how):
     """Under ThreadSanitizer every read of a slot another lane or warp wrote
-    (plans, flat-step descriptors and keys, the CTA's reduction words) must
-    be ordered by the warp or CTA barrier the device code places; an
-    unordered one is reported as a race."""
+    (plans, flat-step descriptors and keys, the CTA's reduction words, the
+    boards of steps shared with idle warps) must be ordered by the warp or
+    CTA barrier or the atomics the device code places; an unordered one is
+    reported as a race."""
     exe, d = emu_tsan
+    env = dict(os.environ)
+    if how == "help":               # every lone flat step shared
+        env["HS_EMU_HELP_MIN"] = "1"
+        how = ""
     rng = np.random.default_rng(3)
     db = mixed_db(rng, 60, [2100], extra=(0, 2))
     q = synth.residues(rng, 50)
@@ -289,7 +298,8 @@ def test_shared_memory_traffic_is_ordered(emu_tsan, how):
         f.write(np.ascontiguousarray(db.codes, np.uint8).tobytes())
         f.write(np.ascontiguousarray(db.offsets, np.int64).tobytes())
         f.write(np.ascontiguousarray(q, np.uint8).tobytes())
-    r = subprocess.run([exe, inp, out] + ([how] if how else []), capture_output=True, text=True, timeout=900)
+    r = subprocess.run([exe, inp, out] + ([how] if how else []), capture_output=True, text=True, timeout=900,
+                       env=env)
     assert r.returncode == 0, r.stderr[-3000:]
     assert "WARNING: ThreadSanitizer" not in r.stderr, r.stderr[:4000]
 
@@ -315,6 +325,19 @@ def test_random_configurations(emu, case):
     flat = None if case % 3 == 0 else (int(rng.choice([1, 4, 16, 64, 100000])), int(rng.choice([1, 32, 128, 100000])))
     check(emu, db, synth.residues(rng, qlen), M, p, int(rng.integers(0, 2**63)), warps=int(rng.integers(1, 4)),
           flat=flat)
+
+
+@pytest.mark.parametrize("help_min,warps,qlen", [(1, 3, 60), (16, 4, 200), (64, 2, 20), (1, 4, 1)])
+def test_idle_warps_share_lone_steps(emu, help_min, warps, qlen):
+    """The end of a scan: a warp left with one pair publishes each of its
+    flat steps with at least help_min units, the CTA's warps that ran out
+    of pairs take passes of it, and the owner waits for them before it
+    consumes the step.  Scores and cell counts must equal the oracle's,
+    every warp must leave, and no wait may run out."""
+    rng = np.random.default_rng(70 + help_min + warps)
+    db = mixed_db(rng, 50, [3100])              # one long pair outlasts the short ones
+    check(emu, db, synth.residues(rng, qlen), O.blosum62(), O.paper_params(rounds=2), 5, warps=warps,
+          help_min=help_min)
 
 
 @pytest.mark.parametrize("lanes", [1, 3, 17])
