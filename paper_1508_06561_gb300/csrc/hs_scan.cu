@@ -167,7 +167,7 @@ struct FlatSlots {
 
 // Sharing between the warps of one CTA: every warp's slots and board (warp
 // w's at slots + w, boards + w), the warps still working on pairs of their
-// own, and the status word a wait that runs out records HS_EINTERNAL in.
+// own, and the status word a wait that runs out records HS_ETIMEOUT in.
 struct Help {
     FlatSlots *slots;
     HelpBoard *boards;
@@ -216,7 +216,7 @@ __device__ __forceinline__ void help_pass(HelpBoard &bd, const uint4 &d, unsigne
 
 __device__ __forceinline__ void help_fail(const Help *hp)
 {
-    if (hp->status) atomicCAS(hp->status, (int32_t)HS_OK, (int32_t)HS_EINTERNAL);
+    if (hp->status) atomicCAS(hp->status, (int32_t)HS_OK, (int32_t)HS_ETIMEOUT);
 }
 
 // The owner's side: publish the lone flat step (slot 0), take passes like
@@ -549,7 +549,7 @@ __device__ __forceinline__ void run_full_items(const DbView &db, const SParams &
 struct ScanQueue {
     int64_t begin, long_end, end;
     unsigned *ctr;
-    int32_t *status;                // HS_EINTERNAL if a wait between warps runs out
+    int32_t *status;                // HS_ETIMEOUT if a wait between warps runs out
     unsigned long long *items;      // full-slide mode: (position, round) items handed out
     int64_t smem_words;             // profile words staged into shared memory
     int rev_off, fwd_off;           // word offsets of the two role profiles

@@ -50,39 +50,63 @@ __global__ void __launch_bounds__(kSortThreads) radix_count_kernel(const uint32_
     hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// In-place exclusive prefix sum of m counts by one block, 1024 at a time.
-__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(uint32_t *a, int64_t m)
+// Prefix sums of m values by one block: each thread takes kScanItems
+// consecutive values, the block scans the threads' totals (warp shuffles,
+// then one warp over the warp totals), and each thread walks its own values
+// calling store(i, sum of the values before i, value i).  A thread reads all
+// of its values before it stores, so store may overwrite in[i].
+constexpr int kScanItems = 16;
+
+template <class In, class Sum, class Store>
+__device__ __forceinline__ void block_prefix(const In *in, int64_t m, Store store)
 {
-    __shared__ uint32_t warp_sum[kScanThreads / 32];
-    __shared__ uint32_t carry;
+    __shared__ Sum warp_sum[kScanThreads / 32];
+    __shared__ Sum carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < m; base += kScanThreads) {
-        const int64_t i = base + threadIdx.x;
-        const uint32_t v = i < m ? a[i] : 0u;
-        uint32_t x = v;
+    for (int64_t base = 0; base < m; base += (int64_t)kScanThreads * kScanItems) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kScanItems;
+        Sum v[kScanItems];
+        Sum t = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            v[k] = i0 + k < m ? (Sum)in[i0 + k] : (Sum)0;
+            t += v[k];
+        }
+        Sum x = t;
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            const Sum y = __shfl_up_sync(0xFFFFFFFFu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_sum[warp] = x;
         __syncthreads();
         if (warp == 0) {
-            uint32_t w = warp_sum[lane];
+            Sum w = warp_sum[lane];
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                const Sum y = __shfl_up_sync(0xFFFFFFFFu, w, o);
                 if (lane >= o) w += y;
             }
             warp_sum[lane] = w;                     // inclusive over warps
         }
         __syncthreads();
-        const uint32_t before = carry + (warp ? warp_sum[warp - 1] : 0u);
-        if (i < m) a[i] = before + x - v;
-        __syncthreads();                            // every thread has read carry
-        if (threadIdx.x == kScanThreads - 1) carry = before + x;
+        Sum run = carry + (warp ? warp_sum[warp - 1] : (Sum)0) + x - t;
+        const Sum next_carry = carry + warp_sum[kScanThreads / 32 - 1];
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            if (i0 + k < m) store(i0 + k, run, v[k]);
+            run += v[k];
+        }
+        __syncthreads();                            // every thread has read carry and warp_sum
+        if (threadIdx.x == 0) carry = next_carry;
         __syncthreads();
     }
+}
+
+// In-place exclusive prefix sum of m counts by one block.
+__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(uint32_t *a, int64_t m)
+{
+    block_prefix<uint32_t, uint32_t>(a, m, [&](int64_t i, uint32_t before, uint32_t) { a[i] = before; });
 }
 
 // Scatter one tile in index order to its digits' positions (stable).
@@ -132,35 +156,8 @@ __global__ void sorted_lengths_kernel(const int64_t *offsets, const int32_t *ord
 // cumres[0] = 0, cumres[i + 1] = cumres[i] + len[i], by one block.
 __global__ void __launch_bounds__(kScanThreads) residue_prefix_kernel(const int32_t *len, int64_t n, int64_t *cumres)
 {
-    __shared__ int64_t warp_sum[kScanThreads / 32];
-    __shared__ int64_t carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) { carry = 0; cumres[0] = 0; }
-    __syncthreads();
-    for (int64_t base = 0; base < n; base += kScanThreads) {
-        const int64_t i = base + threadIdx.x;
-        int64_t x = i < n ? len[i] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t w = warp_sum[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
-                if (lane >= o) w += y;
-            }
-            warp_sum[lane] = w;
-        }
-        __syncthreads();
-        const int64_t incl = carry + (warp ? warp_sum[warp - 1] : 0) + x;
-        if (i < n) cumres[i + 1] = incl;
-        __syncthreads();
-        if (threadIdx.x == kScanThreads - 1) carry = incl;
-        __syncthreads();
-    }
+    if (threadIdx.x == 0) cumres[0] = 0;
+    block_prefix<int32_t, int64_t>(len, n, [&](int64_t i, int64_t before, int64_t v) { cumres[i + 1] = before + v; });
 }
 
 }  // namespace

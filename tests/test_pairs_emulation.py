@@ -347,3 +347,47 @@ def test_warps_filling_only_some_lanes(emu, lanes):
     rng = np.random.default_rng(60 + lanes)
     db = mixed_db(rng, 120, [2048, 2100])
     check(emu, db, synth.residues(rng, 70), O.blosum62(), O.paper_params(rounds=2), 3, warps=3, lanes=lanes)
+
+
+@pytest.fixture(scope="module")
+def help_emu(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("help_emu")
+    with open(d / "hs_pairs_region.inc", "w") as f:
+        f.write(pair_loop_source())
+    exe = str(d / "help_emu")
+    subprocess.check_call([gxx, "-O2", "-std=c++17", "-pthread", "-Wno-unknown-pragmas",
+                           "-I", os.path.join(ROOT, "tests", "emu"), "-I", str(d), "-I", CSRC,
+                           "-I", os.path.join(ROOT, "include"), "-o", exe,
+                           os.path.join(ROOT, "tests", "emu", "help_emu.cpp")])
+    return exe
+
+
+def run_help(exe, how, seed):
+    r = subprocess.run([exe, how, str(seed)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    f = r.stdout.split()
+    return {f[i]: float(f[i + 1]) for i in range(0, len(f), 2)}
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_shared_step_key_with_a_helper(help_emu, seed):
+    """A step shared by its owner and one helper warp: the folded key is the
+    maximum of the units' keys, both warps leave, the status stays OK."""
+    r = run_help(help_emu, "ok", seed)
+    assert r["key"] == r["want"] and r["status"] == 0 and r["live"] == 0
+
+
+def test_owner_gives_up_on_a_pass_that_never_finishes(help_emu):
+    """A helper that claims a pass and never finishes it (made on the host:
+    a stand-in thread that stops after its claim): the owner's wait runs out
+    after its 2 s limit, it records HS_ETIMEOUT (5) and returns."""
+    for seed in range(5):                       # the stand-in must win a claim before the owner takes them all
+        r = run_help(help_emu, "stuck", seed)
+        if r["claimed"]:
+            break
+    assert r["claimed"] == 1
+    assert r["status"] == 5
+    assert 2000 <= r["ms"] < 20000
