@@ -1090,6 +1090,7 @@ struct ReplayArgs {
     int64_t ops_cap;
     int64_t *ops_used;
     int32_t *status;
+    int32_t stage;                  // kReplayStep: copy the hit's role profile into shared memory first
 };
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
@@ -1137,6 +1138,18 @@ __global__ void __launch_bounds__(replay_warps<kForm>() * 32) replay_kernel(DbVi
         c.qsmall = c.tlen >= sp.qlen;
         c.prof = prof + (c.qsmall ? 0 : profile_words(sp.qlen));
         c.S = profile_stride(sp.qlen);
+        if constexpr (kForm == kReplayStep) {
+            // a hit's steps run one after another, each reading profile
+            // words: from shared memory they do not wait on L1/L2 misses
+            if (ra.stage) {
+                extern __shared__ uint4 rsm[];
+                const int64_t n16 = profile_words(sp.qlen) / 4;
+                const uint4 *src = reinterpret_cast<const uint4 *>(c.prof);
+                for (int64_t x = threadIdx.x; x < n16; x += blockDim.x) rsm[x] = src[x];
+                __syncthreads();
+                c.prof = reinterpret_cast<const uint32_t *>(rsm);
+            }
+        }
         int64_t cells = 0;
         int br = 0;
         OpWriter ow;
@@ -1245,14 +1258,25 @@ __global__ void __launch_bounds__(replay_warps<kForm>() * 32) replay_kernel(DbVi
 
 // One CTA per hit when its rounds or (one round, database form) its steps
 // can be shared by the CTA's warps; one warp per hit otherwise.
-static void launch_replay_form(const DbView &db, const SParams &sp, const ReplayArgs &ra, int64_t total,
-                               cudaStream_t st)
+// The one-round CTA form stages the hit's role profile in shared memory
+// when one role of the longest query fits in 96 KB (queries up to ~1,000
+// letters); in the 24-warp rounds form the copy loop cost 200 B of spills.
+static void launch_replay_form(const DbView &db, const SParams &sp, const ReplayArgs &ra0, int64_t total,
+                               int32_t max_qlen, cudaStream_t st)
 {
-    if (sp.rounds > 1)
+    ReplayArgs ra = ra0;
+    const size_t stage_bytes = (size_t)profile_words(max_qlen) * 4;
+    ra.stage = stage_bytes <= 96 * 1024;
+    const size_t smem = ra.stage ? stage_bytes : 0;
+    int per_sm = 0;
+    if (sp.rounds > 1) {
+        ra.stage = 0;
         replay_kernel<kReplayRounds><<<(int)total, kReplayRoundWarps * 32, 0, st>>>(db, sp, ra);
-    else if (sp.mode == HS_MODE_DB && ra.hit_score)
-        replay_kernel<kReplayStep><<<(int)total, kWarpsPerCta * 32, 0, st>>>(db, sp, ra);
-    else
+    } else if (sp.mode == HS_MODE_DB && ra.hit_score) {
+        if (ra.stage && launch_fit(reinterpret_cast<const void *>(replay_kernel<kReplayStep>), kWarpsPerCta * 32,
+                                   smem, &per_sm) != cudaSuccess) ra.stage = 0;
+        replay_kernel<kReplayStep><<<(int)total, kWarpsPerCta * 32, ra.stage ? smem : 0, st>>>(db, sp, ra);
+    } else
         replay_kernel<kReplayWarp><<<(int)((total + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32, 0, st>>>(
             db, sp, ra);
 }
@@ -1286,7 +1310,7 @@ cudaError_t launch_replay(const DbView &db, const uint8_t *d_query, const KParam
     ra.ops_cap = ops_cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    launch_replay_form(db, kp.s, ra, nhits, st);
+    launch_replay_form(db, kp.s, ra, nhits, kp.s.qlen, st);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -1315,7 +1339,7 @@ cudaError_t launch_replay_batch(const DbView &db, const KParams &kp, const Batch
     ra.ops_used = d_ops_used;
     ra.status = d_status;
     const int64_t total = (int64_t)bl.nq * nhits;
-    launch_replay_form(db, kp.s, ra, total, st);
+    launch_replay_form(db, kp.s, ra, total, bl.max_qlen, st);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -1344,7 +1368,7 @@ cudaError_t launch_replay_one(const DbView &db, const uint8_t *d_query, const KP
     ra.ops_cap = cap;
     ra.ops_used = d_ops_used;
     ra.status = d_status;
-    launch_replay_form(db, kp.s, ra, 1, st);
+    launch_replay_form(db, kp.s, ra, 1, kp.s.qlen, st);
     return cudaGetLastError();
 }
 
