@@ -812,6 +812,47 @@ __device__ __forceinline__ void full_scan(const uint32_t *prof, int R, int qlen,
     else full_scan_t<false>(prof, R, qlen, g, bias, flush, lane, vmax, kstar);
 }
 
+// A flat full-slide step as its units see it, 16 bytes: the target base (two
+// words), stored column base | ss << 16, ls | qsmall << 16.  Flat full-slide
+// steps have ls + ss - 1 <= 65535, so ls, ss and k + ss - 1 fit 16 bits.
+__device__ __forceinline__ uint4 full_desc(const Plan &g, int qlen)
+{
+    uint4 d = flat_desc(g, qlen);
+    d.w = (uint32_t)g.ls | ((uint32_t)g.qsmall << 16);
+    return d;
+}
+
+// The key of chunk k0 (shifts k0 .. k0 + 3 of -(ss-1) .. ls-1) of a flat
+// full-slide step: the largest over its shifts k < ls of
+// ((V(k) + bias * ss) << 16) | (0xFFFF - (k + ss - 1)).  V(k) + bias * ss
+// lies in [0, range * ss] when the matrix has a non-negative entry (bias <=
+// range), so with 16-bit pair sums it fits 16 bits; the largest key over a
+// step's chunks is the best V with the lowest k (F1).
+__device__ __forceinline__ uint32_t full_desc_key(const uint32_t *prof_rev, const uint32_t *prof_fwd, int R, int qlen,
+                                                  const uint4 &d, int k0, int bias, int flush)
+{
+    Plan g;
+    g.t = reinterpret_cast<const uint8_t *>(((uint64_t)d.y << 32) | d.x);
+    g.qsmall = (int32_t)(d.w >> 16);
+    g.ls = (int32_t)(d.w & 0xFFFFu);
+    g.ss = (int32_t)(d.z >> 16);
+    const int col = (int)(d.z & 0xFFFFu);
+    if (g.qsmall) { g.Lp = 0; g.Sp = qlen + 3 - col; }     // tb = t + Lp, column base qlen + 3 - Sp
+    else { g.Sp = 0; g.Lp = col - 4; }                      // tb = t + Sp, column base Lp + 4
+    Acc<true> A;
+    A.zero();
+    full_chunk<true>(g.qsmall ? prof_rev : prof_fwd, R, qlen, g, k0, 0, 0, flush, A);
+    uint32_t key = 0u;
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+        const int k = k0 + w;
+        const int32_t v = (int32_t)A.get(w) + bias * (g.ss - full_overlap(g.ls, g.ss, k));
+        const uint32_t kw = ((uint32_t)v << 16) | (0xFFFFu - (uint32_t)(k + g.ss - 1));
+        if (k < g.ls) key = max(key, kw);
+    }
+    return key;
+}
+
 // SCORE (reading A2) kept incrementally over the runs of a growing
 // alignment, in O(1) space.  The gap runs since the last letter pair all
 // share one fate: at the next letter pair they are interior (each maximal

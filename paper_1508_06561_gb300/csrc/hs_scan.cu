@@ -511,6 +511,7 @@ struct FullQueue {
     int64_t begin, end;             // positions [begin, end) of the length order
     unsigned long long *ctr;        // items handed out
     const uint32_t *prof_rev, *prof_fwd;
+    int64_t long_end;               // run_full_pairs: positions [begin, long_end) are taken one item per warp
 };
 
 __device__ __forceinline__ void run_full_items(const DbView &db, const SParams &sp, const FullQueue &qu,
@@ -540,6 +541,169 @@ __device__ __forceinline__ void run_full_items(const DbView &db, const SParams &
             atomicMax(&scores[d], s);
             if (cells_out) atomicAdd(reinterpret_cast<unsigned long long *>(&cells_out[d]), (unsigned long long)cells);
         }
+    }
+}
+
+// Full-slide mode with lane-owned items (16-bit pair sums, a matrix with a
+// non-negative entry): every lane of a warp holds one (position, round)
+// item -- a long pair's rounds sit in neighbouring lanes -- in the database
+// form's lane state plus the round's RunScore (F4).  Each loop round plans
+// one full-slide step per item (F2: ss up to Srem, not ls), deals the chunks
+// of all flat steps over the warp as in run_pairs (ranked by role and trip
+// count, owners from the pass start masks, keys folded by warp maximum or
+// shared atomics: full_desc_key), scans the others warp-wide
+// (full_scan_t), and consumes every step by F3.  A finished round folds
+// its score and cells into the pair's by atomics, as run_full_items does.
+__device__ __forceinline__ void run_full_pairs(const DbView &db, const SParams &sp, const QueryCtx &qc,
+                                               const FullQueue &fq, unsigned lanes, FlatSlots *fs, Plan *plans,
+                                               int lane)
+{
+    const int R = profile_stride(sp.qlen);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned long long rounds = (unsigned)sp.rounds;
+    const unsigned long long items = (unsigned long long)(fq.end - fq.begin) * rounds;
+    const unsigned long long long_items = (unsigned long long)(max(fq.long_end, fq.begin) - fq.begin) * rounds;
+    Lane L = {};
+    L.d = -1;
+    L.t = db.codes;
+    RunScore rs;
+    rs.init();
+    bool open = items > 0;
+    bool alone = long_items > 0;            // a long target's rounds: one per warp, so each has the warp alone
+    for (;;) {
+        if (open) {
+            unsigned need = __ballot_sync(0xFFFFFFFFu, L.d < 0) & lanes;
+            if (alone) need &= 1u;
+            if (need) {
+                const int m = __popc(need);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(fq.ctr, (unsigned long long)m);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base + m >= items) open = false;
+                if (base >= long_items) alone = false;
+                const unsigned long long it = base + (unsigned long long)__popc(need & lt_mask);
+                if (((need >> lane) & 1u) && it < items) {
+                    const unsigned long long pi = it / rounds;
+                    L.d = db.order[fq.begin + (int64_t)pi];
+                    L.round = (int32_t)(it - pi * rounds);
+                    const int64_t off = db.offsets[L.d];
+                    const int32_t tlen = (int32_t)(db.offsets[L.d + 1] - off);
+                    L.t = db.codes + off;
+                    L.qsmall = tlen >= sp.qlen;
+                    L.nl = L.qsmall ? tlen : sp.qlen;
+                    L.ns = L.qsmall ? sp.qlen : tlen;
+                    L.cells = 0;
+                    lane_start_round(L, sp);
+                    rs.init();
+                }
+            }
+        }
+        // a round whose loop has ended (or never began: an empty sequence)
+        // settles: the rest of each sequence against gaps, then the fold
+        if (L.d >= 0 && !(L.Lp < L.nl && L.Sp < L.ns)) {
+            rs.gap(1, L.nl - L.Lp);
+            rs.gap(0, L.ns - L.Sp);
+            rs.finish(sp);
+            atomicMax(&qc.scores[L.d], rs.score);
+            if (qc.cells) atomicAdd(reinterpret_cast<unsigned long long *>(&qc.cells[L.d]), (unsigned long long)L.cells);
+            L.d = -1;
+        }
+        __syncwarp();
+        const bool busy = L.d >= 0;
+        if (__ballot_sync(0xFFFFFFFFu, busy) == 0) {
+            if (!open) break;
+            continue;                       // every held round settled: refill
+        }
+
+        Plan g = {L.t, L.Lp, L.Sp, 1, 1, L.qsmall, 0, 0, 0};
+        bool flat = false;
+        if (busy) {
+            const int32_t Lrem = L.nl - L.Lp, Srem = L.ns - L.Sp;
+            g.ls = max((int32_t)(((uint64_t)Lrem * L.lf) >> 16), 1);
+            const uint64_t u = lane_draw(L, sp, 2 + (uint64_t)L.step);
+            const int64_t ssw = (int64_t)(((uint64_t)Srem * L.sf * u) >> 32);
+            g.ss = (int32_t)max((int64_t)1, min(ssw, (int64_t)Srem));                      // F2
+            const int32_t nchunk = (g.ls + g.ss - 1 + 3) >> 2;
+            const int32_t niter = g.ss + (L.qsmall ? 3 : 0);
+            flat = g.ls + g.ss - 1 <= 65535 && (nchunk >= sp.flat_min_chunks || niter <= sp.flat_max_iters);
+        }
+        int32_t vmax = 0, kstar = 0;
+        {
+            const int units = flat ? (g.ls + g.ss - 1 + 3) >> 2 : 0;
+            const uint32_t iters = (uint32_t)min(g.ss + 3 * g.qsmall, (1 << 24) - 1);
+            uint32_t sk = flat ? ((uint32_t)g.qsmall << 30) | ((0xFFFFFFu - iters) << 5) | (uint32_t)lane
+                               : 0x80000000u | (uint32_t)lane;
+            for (int k = 2; k <= 32; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, sk, j);
+                    const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+                    sk = take_min ? min(sk, o) : max(sk, o);
+                }
+            }
+            const int src = (int)(sk & 31u);
+            const int ru = __shfl_sync(0xFFFFFFFFu, units, src);
+            int incl = ru;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            fs->rank[src] = lane;
+            fs->key[lane] = 0u;
+            __syncwarp();
+            const int slot = fs->rank[lane];
+            if (flat) fs->desc[slot] = full_desc(g, sp.qlen);
+            else if (busy) plans[lane] = g;
+            __syncwarp();
+            const int my_u0 = incl - ru;
+            int carry = -1, carry_u0 = 0;
+            for (int base = 0; base < total; base += 32) {
+                const int u = base + lane;
+                const bool valid = u < total;
+                uint32_t key = 0u;
+                const unsigned starts = __reduce_or_sync(0xFFFFFFFFu, start_bit(my_u0, ru, base));
+                const int owner = pass_owner(carry, starts, lane);
+                const int first = pass_first_unit(carry_u0, starts, base, lane);
+                carry_u0 = pass_first_unit(carry_u0, starts, base, 31);
+                carry = pass_owner(carry, starts, 31);
+                if (valid) {
+                    const uint4 d = fs->desc[owner];
+                    const int ss = (int)(d.z >> 16);
+                    key = full_desc_key(qc.prof_rev, qc.prof_fwd, R, sp.qlen, d, 4 * (u - first) - (ss - 1),
+                                        sp.bias, sp.flush);
+                }
+                fold_keys(fs, starts, owner, valid, key, lane);
+            }
+            __syncwarp();
+            if (flat) {
+                const uint32_t key = fs->key[slot];
+                vmax = (int32_t)(key >> 16) - sp.bias * g.ss;
+                kstar = (int32_t)(0xFFFFu - (key & 0xFFFFu)) - (g.ss - 1);
+            }
+        }
+        // the other steps, one item at a time, by the whole warp
+        unsigned coop = __ballot_sync(0xFFFFFFFFu, busy && !flat);
+        while (coop) {
+            const int i = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const Plan h = plans[i];
+            int32_t v, k;
+            full_scan_t<true>(h.qsmall ? qc.prof_rev : qc.prof_fwd, R, sp.qlen, h, sp.bias, sp.flush, lane, v, k);
+            if (lane == i) { vmax = v; kstar = k; }
+        }
+        // consume (F3: leading overhang, overlap, trailing overhang of small)
+        if (busy) {
+            L.cells += (int64_t)g.ls * g.ss;
+            const int32_t j0 = max(0, -kstar), j1 = min(g.ss, g.ls - kstar);
+            rs.gap(0, j0);
+            rs.gap(1, max(kstar, 0));
+            rs.match(vmax, sp);
+            rs.gap(0, g.ss - j1);
+            L.Lp += kstar + j1;
+            L.Sp += g.ss;
+            L.step++;
+        }
+        __syncwarp();
     }
 }
 
@@ -732,8 +896,35 @@ scan_full_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, S
         __syncthreads();
         prof = reinterpret_cast<const uint32_t *>(smem_raw);
     }
-    const FullQueue fq = {qu.begin, qu.end, qu.items, prof + qu.rev_off, prof + qu.fwd_off};
+    const FullQueue fq = {qu.begin, qu.end, qu.items, prof + qu.rev_off, prof + qu.fwd_off, qu.begin};
     run_full_items(db, sp, fq, scores, cells_out, threadIdx.x & 31);
+}
+
+// Full-slide mode, lane-owned items (run_full_pairs).
+template <bool kSmem>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 2)
+scan_full_lanes_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ prof_g, SParams sp,
+                       int32_t *__restrict__ scores, int64_t *__restrict__ cells_out)
+{
+    extern __shared__ uint4 smem_raw[];
+    __shared__ Plan plans[kWarpsPerCta][32];
+    __shared__ FlatSlots flat_slots[kWarpsPerCta];
+    const uint32_t *prof = prof_g;
+    if (kSmem) {
+        const int64_t n16 = qu.smem_words / 4;
+        const uint4 *src = reinterpret_cast<const uint4 *>(prof_g);
+        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) smem_raw[i] = src[i];
+        __syncthreads();
+        prof = reinterpret_cast<const uint32_t *>(smem_raw);
+    }
+    QueryCtx qc;
+    qc.prof_rev = prof + qu.rev_off;
+    qc.prof_fwd = prof + qu.fwd_off;
+    qc.scores = scores;
+    qc.cells = cells_out;
+    const FullQueue fq = {qu.begin, qu.end, qu.items, qc.prof_rev, qc.prof_fwd, qu.long_end};
+    const int w = threadIdx.x >> 5;
+    run_full_pairs(db, sp, qc, fq, qu.lanes, &flat_slots[w], plans[w], threadIdx.x & 31);
 }
 
 size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
@@ -795,6 +986,11 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         e = cudaEventRecord(trace->start, st);
         if (e != cudaSuccess) return e;
     }
+    // full-slide mode: lane-owned items need 16-bit pair sums and a matrix
+    // with a non-negative entry (full_desc_key's range); else one item per warp
+    int8_t mmax = -128;
+    for (int i = 0; i < kNSym * kNSym; i++) mmax = max(mmax, kp.m[i]);
+    const bool full_lanes = kp.s.pair16 != 0 && mmax >= 0;
     for (int i = 0; i < nq; i++) {
         qs[i].items = reinterpret_cast<unsigned long long *>(ws.counters + (i == 0 ? kFullItems0 : kFullItems1));
         qs[i].status = d_status;
@@ -803,7 +999,8 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         // length order: one CTA per SM, the widest whose profile(s) and slots fit
         const int wide = kp.s.mode != HS_MODE_FULL && staged && !input_order ? wide_warps(qs[i].smem_words) : 0;
         const ScanKernelFn kern = kp.s.mode == HS_MODE_FULL
-                                      ? (staged ? scan_full_kernel<true> : scan_full_kernel<false>)
+                                      ? (full_lanes ? (staged ? scan_full_lanes_kernel<true> : scan_full_lanes_kernel<false>)
+                                                    : (staged ? scan_full_kernel<true> : scan_full_kernel<false>))
                                       : wide ? pick_wide_kernel(wide, kp.s.pair16 != 0, share_steps)
                                              : pick_scan_kernel(staged, kp.s.pair16 != 0);
         if (wide) smem += wide * (kWarpSlotBytes + kHelpSlotBytes) + kCtaSlotBytes;
@@ -812,7 +1009,12 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         e = launch_fit(reinterpret_cast<const void *>(kern), threads, smem, &per_sm);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        qs[i].lanes = lanes_for(qs[i].end - qs[i].begin, (int64_t)per_sm * num_sms * (threads / 32));
+        // full-slide items: about four handed to each warp over the scan, so
+        // that warps refill and balance (a flat step's units still fill all
+        // 32 lanes)
+        const bool full = kp.s.mode == HS_MODE_FULL;
+        const int64_t work = (qs[i].end - qs[i].begin) * (full ? kp.s.rounds : 1);
+        qs[i].lanes = lanes_for(work, (int64_t)per_sm * num_sms * (threads / 32) * (full ? 4 : 1));
         kern<<<per_sm * num_sms, threads, smem, st>>>(db, qs[i], srcs[i], kp.s, ws.scores, d_cells);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

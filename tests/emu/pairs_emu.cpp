@@ -19,7 +19,10 @@
 // int32 ops count, int32 span[4] (q begin, q end, t begin, t end) and the
 // ops.
 //
-// usage: pairs_emu IN OUT [whole|cta|ops|ops_cta]
+// With "lanes" (full-slide mode, 16-bit pair sums), every lane holds one
+// (position, round) item (run_full_pairs).
+//
+// usage: pairs_emu IN OUT [whole|lanes|cta|ops|ops_cta]
 //   IN  (little-endian): int64 n, int64 nres, int32 qlen, int32 warps,
 //       int32 pgp, gop, gep, rounds, mode, uint32 lf_q16, sf_q16, minf_q16,
 //       uint64 seed, int64 index_base, int8 M[24*24] (M[query][target]),
@@ -74,7 +77,7 @@ static void run_full(const DbView &db, const SParams &sp, const QueryCtx &qc, co
     std::fill(qc.scores, qc.scores + db.n, INT_MIN);
     std::fill(qc.cells, qc.cells + db.n, 0);
     unsigned long long ctr = 0;
-    const FullQueue fq = {pq.begin, pq.end, &ctr, qc.prof_rev, qc.prof_fwd};
+    const FullQueue fq = {pq.begin, pq.end, &ctr, qc.prof_rev, qc.prof_fwd, pq.begin};
     std::vector<EmuWarp> ws(warps);
     std::vector<std::thread> th;
     for (int w = 0; w < warps; w++)
@@ -83,6 +86,28 @@ static void run_full(const DbView &db, const SParams &sp, const QueryCtx &qc, co
                 emu_warp = &ws[w];
                 emu_lane = lane;
                 run_full_items(db, sp, fq, qc.scores, qc.cells, lane);
+            });
+    for (auto &t : th) t.join();
+}
+
+// the full-slide scan's lane-owned form: every lane holds a (position,
+// round) item, the warp's flat steps dealt as units (run_full_pairs)
+static void run_full_lanes(const DbView &db, const SParams &sp, const QueryCtx &qc, const PosQueue &pq, int warps)
+{
+    std::fill(qc.scores, qc.scores + db.n, INT_MIN);
+    std::fill(qc.cells, qc.cells + db.n, 0);
+    unsigned long long ctr = 0;
+    const FullQueue fq = {pq.begin, pq.end, &ctr, qc.prof_rev, qc.prof_fwd, pq.long_end};
+    std::vector<EmuWarp> ws(warps);
+    std::vector<Plan> plans((size_t)warps * 32);
+    std::vector<FlatSlots> slots(warps);
+    std::vector<std::thread> th;
+    for (int w = 0; w < warps; w++)
+        for (int lane = 0; lane < 32; lane++)
+            th.emplace_back([&, w, lane] {
+                emu_warp = &ws[w];
+                emu_lane = lane;
+                run_full_pairs(db, sp, qc, fq, pq.lanes, &slots[w], plans.data() + 32 * w, lane);
             });
     for (auto &t : th) t.join();
 }
@@ -239,7 +264,7 @@ static void run_replay(const DbView &db, const SParams &sp, const QueryCtx &qc, 
 
 int main(int argc, char **argv)
 {
-    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole|cta|ops|ops_cta]\n"); return 2; }
+    if (argc != 3 && argc != 4) { fprintf(stderr, "usage: pairs_emu IN OUT [whole|lanes|cta|ops|ops_cta]\n"); return 2; }
     const std::string how = argc == 4 ? argv[3] : "";
     FILE *f = fopen(argv[1], "rb");
     if (!f) return 2;
@@ -323,6 +348,7 @@ int main(int argc, char **argv)
         return 0;
     }
     if (how == "whole") run_whole(db, sp, qc, pq, warps);
+    else if (how == "lanes") run_full_lanes(db, sp, qc, pq, warps);
     else if (how == "cta") run_cta(db, sp, qc, pq, warps);
     else if (sp.pair16) run<true>(db, sp, qc, pq, warps);
     else run<false>(db, sp, qc, pq, warps);

@@ -195,6 +195,23 @@ def test_full_slide_items_both_roles(emu, matrix, qlen):
     check(emu, db, synth.residues(rng, qlen), M, p, 21, warps=3, how="whole")
 
 
+@pytest.mark.parametrize("matrix,qlen,lanes,flat", [("blosum62", 60, None, None), ("blosum62", 300, 5, None),
+                                                    ("wide", 90, None, (1, 100000)), ("blosum62", 40, None, (100000, 1)),
+                                                    ("blosum62", 1, 3, None)])
+def test_full_slide_lane_owned_items(emu, matrix, qlen, lanes, flat):
+    """Full-slide mode with every lane holding one (pair, round) item and the
+    warp's flat steps dealt as units (run_full_pairs, F1-F4): both roles,
+    overhanging steps, several rounds of a long pair in neighbouring lanes,
+    warps filling only some lanes, every step flat and none flat, a wide
+    matrix (byte sums widened every few cells)."""
+    rng = np.random.default_rng(90 + qlen)
+    M = O.blosum62() if matrix == "blosum62" else synth.random_symmetric_matrix(rng, -40, 50)
+    db = mixed_db(rng, 60, [2300])
+    p = O.paper_params(rounds=6, mode=O.MODE_FULL, sfactor_q16=65536, lfactor_q16=45000, minfactor_q16=10000,
+                       pgp=1)
+    check(emu, db, synth.residues(rng, qlen), M, p, 31, warps=3, how="lanes", lanes=lanes, flat=flat)
+
+
 @pytest.mark.parametrize("matrix", ["blosum62", "full-range"])
 def test_one_cta_per_pair(emu, matrix):
     """align_round_cta: every step of a pair scanned by all warps of a CTA,
@@ -273,7 +290,7 @@ def emu_tsan(tmp_path_factory):
     return exe, d
 
 
-@pytest.mark.parametrize("how", ["", "help", "cta", "ops_cta"])
+@pytest.mark.parametrize("how", ["", "help", "lanes", "cta", "ops_cta"])
 def test_shared_memory_traffic_is_ordered(emu_tsan, how):
     """Under ThreadSanitizer every read of a slot another lane or warp wrote
     (plans, flat-step descriptors and keys, the CTA's reduction words, the
@@ -288,7 +305,7 @@ def test_shared_memory_traffic_is_ordered(emu_tsan, how):
     rng = np.random.default_rng(3)
     db = mixed_db(rng, 60, [2100], extra=(0, 2))
     q = synth.residues(rng, 50)
-    p = O.paper_params()
+    p = O.paper_params(rounds=3, mode=O.MODE_FULL) if how == "lanes" else O.paper_params()
     hdr = struct.pack("<qqiiiiiiiIIIQq", db.n, len(db.codes), len(q), 2, p.pgp, p.gop, p.gep, p.rounds, p.mode,
                       p.lfactor_q16, p.sfactor_q16, p.minfactor_q16, 1, 0)
     inp, out = str(d / "in.bin"), str(d / "out.bin")
