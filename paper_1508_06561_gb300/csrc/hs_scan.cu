@@ -960,7 +960,10 @@ cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const
         q.smem_words = fuse_roles(kp.s.qlen) ? 2 * words : 0;
         q.rev_off = 0; q.fwd_off = (int)words;
         srcs[nq++] = ws.prof;
-    } else if (fuse_roles(kp.s.qlen)) {
+    } else if (kp.s.mode == HS_MODE_FULL ? fuse_roles(kp.s.qlen) : wide_warps(2 * words) == 24) {
+        // database form: both role profiles in one launch whenever they fit
+        // beside 24 warps' slots (queries up to ~940 letters); the
+        // full-slide kernels run several CTAs per SM and keep the 100 KB rule
         ScanQueue &q = qs[nq];
         q.begin = 0; q.end = db.n; q.long_end = min(long_end, split);
         q.ctr = ws.counters + kQsLong;
