@@ -929,7 +929,8 @@ scan_full_lanes_kernel(DbView db, ScanQueue qu, const uint32_t *__restrict__ pro
 
 size_t scan_smem_bytes(int32_t qlen) { return (size_t)profile_words(qlen) * 4; }
 
-// Both profiles share one launch when they fit twice per SM with room to spare.
+// Several-CTA-per-SM kernels (database order, full-slide mode): both
+// profiles share one launch when they fit twice per SM with room to spare.
 static bool fuse_roles(int32_t qlen) { return 2 * scan_smem_bytes(qlen) <= 100 * 1024; }
 
 cudaError_t launch_scan(const DbView &db, int64_t split, int64_t long_end, const uint8_t *d_query,
