@@ -172,7 +172,10 @@ int64_t hs_ops_capacity(int32_t qlen, int32_t k);
  *   d_status    : device int32 receiving HS_OK or the first device-side error.
  *                 A letter code >= 24 in d_query (which the host cannot
  *                 see) is reported here as HS_EINVAL; that column scores 0
- *                 and no memory outside the buffers is read.
+ *                 and no memory outside the buffers is read.  HS_ETIMEOUT:
+ *                 a wait between the scan's warps ran out (databases with
+ *                 many targets of 8,192+ letters share a long pair's steps
+ *                 with idle warps at the scan's end; never expected).
  * Host-side argument errors are returned before anything is enqueued. */
 int hs_search_device(const hs_db *db, const uint8_t *d_query, int32_t qlen,
                      const hs_params *p, int32_t k, uint64_t seed, void *stream,
