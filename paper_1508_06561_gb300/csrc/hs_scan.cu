@@ -1,6 +1,7 @@
 // hs_scan.cu -- the database scan (every pair's score) and the alignment
-// replay of the ranked hits.  Database-search form of Fig. 1 (Sec. III.B.3),
-// for one query (plain) or many (batched).
+// replay of the ranked hits: the database-search form of Fig. 1
+// (Sec. III.B.3) for one query (plain) or many (batched), and the
+// full-slide form (Fig. 1 as printed, several rounds).
 #include <cuda_runtime.h>
 
 #include <map>
@@ -70,12 +71,17 @@ __global__ void profile_kernel(ProfileJob job, KParams kp)
 // best round, size factors, one cached Philox block -- sits in that lane's
 // registers, so the step bookkeeping of 32 pairs runs as one SIMT
 // instruction stream.  Each round of the loop plans one step for every held
-// pair.  Small steps (at most kLocalIters chunk iterations) are scored by
-// their own lane; the others one at a time by the whole warp (coop_scan),
-// reading the step's plan from the warp's shared-memory plan slots.
-// Positions come from a queue over the length-ordered database (longest
-// first); targets of >= kLongLen letters are taken one per warp (only lane 0
-// holds a pair) so each gets the warp alone.
+// pair.  With 16-bit pair sums the chunks of every step that joins the flat
+// list are dealt to the warp's 32 lanes as units (see run_pairs); the other
+// steps (few long chunks) are scanned one at a time by the whole warp on a
+// lane grid (coop_scan_t), reading the step's plan from the warp's
+// shared-memory plan slots.  With 32-bit sums (wide matrices) small steps
+// (at most kLocalIters chunk iterations) are scored by their own lane and
+// the rest on the lane grid.  Positions come from a queue over the
+// length-ordered database (longest first); targets of >= kLongLen letters
+// are taken one per warp (only lane 0 holds a pair) so each gets the warp
+// alone.  The full-slide mode's loops (run_full_items, run_full_pairs)
+// follow at the end of this part.
 // ---------------------------------------------------------------------------
 constexpr int kLocalIters = 64;
 // flattened scan (16-bit pair sums): a step joins the unit list when it has
@@ -1269,10 +1275,10 @@ cudaError_t launch_scan_batch(const DbView &db, const int64_t *d_cumres, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Replay of the ranked hits.  One warp per hit reruns the pair with the same
-// draws (so the scan itself never stores an alignment), checks the score
-// against the scan's, and writes the winning round's run-length ops into the
-// hit's slot.  The last CTA to finish packs the slots into the caller's ops
+// Replay of the ranked hits.  A CTA (or a warp) per hit reruns the pair with
+// the same draws (so the scan itself never stores an alignment), checks the
+// score against the scan's, and writes the winning round's run-length ops
+// into the hit's slot.  The last CTA to finish packs the slots into the caller's ops
 // buffer and fills in the offsets.  Batched: hit i belongs to query i / nhits.
 // ---------------------------------------------------------------------------
 struct ReplayArgs {
