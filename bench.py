@@ -152,7 +152,7 @@ def kernel_source_hash():
 
 
 def measured_hbm_gbs():
-    """The machine's measured copy bandwidth, else the documented fallback."""
+    """The measured copy bandwidth (MEASURED_PEAKS.json), else the documented fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"])

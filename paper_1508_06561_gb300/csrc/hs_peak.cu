@@ -1,8 +1,8 @@
 // hs_peak.cu -- integer issue-rate microbenchmarks for the scan's roofline.
 //
 // The scan is bound by integer instruction issue, not by HBM, so its
-// roofline needs the GPU's integer throughput; the copy and GEMM peaks
-// measured for the pool say nothing about it.  These kernels measure it:
+// roofline needs the GPU's integer throughput; a memory-copy rate or a
+// tensor-core GEMM rate says nothing about it.  These kernels measure it:
 // every thread runs eight interleaved dependency chains of one operation
 // (each chain reads the next chain's latest value, so no result is dead and
 // no two operations can be merged into one), enough warps are resident to
