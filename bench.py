@@ -289,6 +289,7 @@ def batched_section(P, D, db, params, seed, reps=3):
     st.synchronize()
     t_plain = a2.elapsed_time(b2) / 1000.0 / reps
     res = db.residues * len(qs)
+    small = batched_small_db(P, qs, params, seed)
     return {"workload": "batched-64q-u30-1000-swissprot-like-570k", "queries": len(qs), "k": k,
             "value": res / t_batch, "unit": UNIT, "ms_per_batch": t_batch * 1000.0,
             "plain_same_queries": res / t_plain, "plain_ms": t_plain * 1000.0,
@@ -296,7 +297,50 @@ def batched_section(P, D, db, params, seed, reps=3):
             "default_tuning": autotune.DEFAULT, "default_ms_per_batch": t_default * 1000.0,
             "tuned_speedup_vs_default": t_default / t_batch, "tuned_output_identical": same,
             "tuning_evaluated": len(tune_s),
-            "tuning_candidates_ms": {kk: v * 1000.0 for kk, v in tune_s.items()}}
+            "tuning_candidates_ms": {kk: v * 1000.0 for kk, v in tune_s.items()},
+            "small_db": small}
+
+
+def batched_small_db(P, qs, params, seed, k=10, reps=20):
+    """The same 64 queries against the 2,000-target database, where one
+    query cannot fill the GPU: one batched call vs one plain search each."""
+    import torch
+
+    from paper_1508_06561_gb300 import synth
+    db, _, _ = synth.plain_small(0)
+    D = P.Database(db.codes, db.offsets)
+    cat = torch.from_numpy(np.concatenate(qs)).cuda()
+    off = np.zeros(len(qs) + 1, np.int64)
+    np.cumsum([len(q) for q in qs], out=off[1:])
+    offd = torch.from_numpy(off).cuda()
+    seeds = torch.full((len(qs),), seed, dtype=torch.int64, device="cuda")
+    mq = int(max(len(q) for q in qs))
+    qd = [torch.from_numpy(q).cuda() for q in qs]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        out = P.search_batch_device(D, cat, offd, seeds, mq, k, params, None, st)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            P.search_batch_device(D, cat, offd, seeds, mq, k, params, None, st, out["workspace"], out)
+        b.record(st)
+        o1 = P.search_device(D, qd[int(np.argmax([len(q) for q in qs]))], k, params, seed=seed, stream=st)
+        for q in qd:
+            P.search_device(D, q, k, params, seed=seed, stream=st, workspace=o1["workspace"], out=o1)
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(st)
+        for _ in range(reps):
+            for q in qd:
+                P.search_device(D, q, k, params, seed=seed, stream=st, workspace=o1["workspace"], out=o1)
+        b2.record(st)
+    st.synchronize()
+    assert int(out["status"].item()) == 0 and int(o1["status"].item()) == 0
+    t_batch = a.elapsed_time(b) / 1000.0 / reps
+    t_plain = a2.elapsed_time(b2) / 1000.0 / reps
+    D.close()
+    res = db.residues * len(qs)
+    return {"workload": "batched-64q-u30-1000-plain-small-2k", "k": k, "value": res / t_batch, "unit": UNIT,
+            "ms_per_batch": t_batch * 1000.0, "plain_ms": t_plain * 1000.0, "speedup_vs_plain": t_plain / t_batch}
 
 
 # --------------------------------------------------------------------------

@@ -233,7 +233,8 @@ int hs_search(hs_db *db, const uint8_t *query, int32_t qlen, const hs_params *p,
  * offsets index one ops buffer shared by all queries.
  * tuning (optional, NULL = defaults; no counterpart in the paper; every
  * field 0 = its default, results never depend on the tuning):
- *   chunks          work items per query over the database (<= 8192; 1024);
+ *   chunks          chunks per query over the database (<= 8192; default:
+ *                   one per ~256 targets, at most 1024);
  *   warps           warps per scan CTA, 24 or 12 (default: the widest that
  *                   fits the class's profile; a value that does not fit is
  *                   ignored);

@@ -3,8 +3,9 @@
 The batched scan's speed, never its results, depends on five knobs
 (hs_batch_tuning):
 
-* chunks -- work items per query over the length-ordered database (fewer:
-  less per-item overhead, longer tails);
+* chunks -- chunks per query over the length-ordered database (fewer:
+  less per-item overhead, longer tails; 0 lets the library pick one per ~256
+  targets, at most 1024);
 * warps -- warps per scan CTA, 24 or 12 (more warps hide more latency;
   fewer leave each warp more registers and the profile more room);
 * flat_min_chunks, flat_max_iters -- which steps go to the flat unit list
@@ -26,7 +27,8 @@ import numpy as np
 
 from . import Database, Params, search_batch_device
 
-DEFAULT = {"chunks": 1024, "warps": 24, "flat_min_chunks": 16, "flat_max_iters": 128, "long_len": 2048}
+# chunks 0: the library's default (one chunk per ~256 targets, at most 1024)
+DEFAULT = {"chunks": 0, "warps": 24, "flat_min_chunks": 16, "flat_max_iters": 128, "long_len": 2048}
 SPACE = {
     "chunks": (256, 512, 1024, 2048, 4096),
     "warps": (24, 12),

@@ -666,7 +666,13 @@ int hs_search_batch_device(const hs_db *db, int32_t nq, const uint8_t *d_queries
     if (max_qlen < 1 || total_qlen < nq) return HS_EINVAL;
     if (max_qlen > HS_MAX_QUERY_LEN) return HS_ETOOLONG;
     if (k < 0 || k > HS_MAX_K || ops_cap < 0) return HS_EINVAL;
-    const int32_t nchunk = tuning && tuning->chunks > 0 ? tuning->chunks : kDefaultChunks;
+    // default: about 256 targets per chunk, at most kDefaultChunks (the
+    // 570k-target database's best); a small database gets a few large
+    // chunks, so that an item is not a handful of pairs behind a profile copy
+    // and a CTA barrier
+    const int32_t nchunk = tuning && tuning->chunks > 0
+                               ? tuning->chunks
+                               : (int32_t)std::max<int64_t>(1, std::min<int64_t>(kDefaultChunks, (db->n + 255) / 256));
     if (nchunk > kMaxChunks) return HS_EINVAL;
     if (tuning && (tuning->warps < 0 || tuning->flat_min_chunks < 0 || tuning->flat_max_iters < 0 ||
                    tuning->long_len < 0))
