@@ -123,6 +123,16 @@ template <class T> inline T __shfl_xor_sync(unsigned, T v, int o) {
     if (!emu_warp) return v;
     return emu_exchange(v, [&](const uint64_t *s) { return emu_get<T>(s[(emu_lane ^ o) & 31]); });
 }
+// lanes whose value equals the calling lane's
+inline unsigned __match_any_sync(unsigned, unsigned v) {
+    if (!emu_warp) return 1u;
+    return emu_exchange(v, [](const uint64_t *s) {
+        unsigned r = 0;
+        const unsigned mine = (unsigned)s[emu_lane];
+        for (int i = 0; i < 32; i++) r |= ((unsigned)s[i] == mine ? 1u : 0u) << i;
+        return r;
+    });
+}
 inline unsigned __ballot_sync(unsigned, int p) {
     if (!emu_warp) return p ? 1u : 0u;
     return emu_exchange(p ? 1u : 0u, [](const uint64_t *s) {
